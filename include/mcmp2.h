@@ -1,0 +1,191 @@
+/*
+ * mcmp2.h -- C ABI of the GB300 Monte Carlo four-component relativistic MP2
+ * library (Cruz, Garza, Yanai, Hirata, arXiv 2203.05632).
+ *
+ * The library evaluates, entirely on one GPU, the per-step Monte Carlo
+ * estimate of the second-order energy of Eq. FinalMP2 in the 13-dimensional
+ * form of Eq. MCMP2 (Sec. III): a Metropolis move of m electron-pair walkers
+ * under w(r1,r2) = g(r1) g(r2) / (N_g r12) (Eq. basisSet), large- and
+ * kinetically balanced small-component basis values at the 2m positions
+ * (Eq. C, Eq. KB), four-component spinors, imaginary times tau from the
+ * inverse CDF of w(tau) = lambda exp(-lambda tau) (Eq. tauWeight), the 4x4
+ * propagator blocks G-(x,y,-tau) and G+(x,y,tau) between all walker pairs,
+ * and the traced direct and exchange products summed over all mC2 pairs of
+ * pairs (Eq. redundant), with Flyvbjerg-Petersen blocking (Eq. uncertainty).
+ *
+ * Conventions for every call:
+ *  - Units are bohr and hartree.  Complex numbers are (re, im) double pairs.
+ *  - Every call returns MCMP2_OK (0) or a negative MCMP2_E* status; no call
+ *    aborts or throws.  mcmp2_last_error() gives the message of the last
+ *    failure on a context.
+ *  - Pointers named *_host are host memory read or written synchronously
+ *    with respect to the context's stream (the call returns after the copy).
+ *  - The context owns no device memory: the caller allocates one device
+ *    workspace of mcmp2_workspace_bytes() bytes, binds it, and keeps it
+ *    alive until mcmp2_destroy().  All work is issued on the stream given at
+ *    creation.
+ *  - A context is not thread-safe; calls on one context must not overlap.
+ *
+ * Readings of the paper fixed by this interface:
+ *  - Basis (Eq. C, Eq. KB, restricted kinetic balance): n_L real Cartesian
+ *    Gaussians g_mu (shells of l = 0, 1, 2 expanded in the order s; x, y, z;
+ *    xx, xy, xz, yy, yz, zz), g_mu(r) = coef (x-Ax)^a (y-Ay)^b (z-Az)^c
+ *    exp(-alpha |r-A|^2).  Large 2-spinor basis {g_mu e_alpha, g_mu e_beta};
+ *    small 2-spinor basis {(sigma.grad)(g_mu e_alpha), (sigma.grad)(g_mu e_beta)}
+ *    (= i(sigma.p) of the large ones).  Spinor coefficients C have 4 n_L rows:
+ *    L-alpha, L-beta, S-alpha, S-beta blocks of n_L rows each.
+ *  - The integrand is the trace form of Eq. MCMP2 derived from Eq. FinalMP2:
+ *    -1/2 { tr[G-(3,1)G+(1,3)] tr[G-(4,2)G+(2,4)] - tr[G-(3,1)G+(1,4)G-(4,2)G+(2,3)] }
+ *    with (r1, r2) = pair p, (r3, r4) = pair q; its real part is summed over p < q.
+ *  - n_tau imaginary times per step are shared by all pairs and averaged.
+ */
+#ifndef MCMP2_H
+#define MCMP2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define MCMP2_OK 0
+#define MCMP2_EINVAL (-1)      /* bad argument, size or state */
+#define MCMP2_ENOTLOADED (-2)  /* system, workspace or walkers missing */
+#define MCMP2_ECUDA (-3)       /* a CUDA call failed (message has the CUDA error) */
+#define MCMP2_ENONFINITE (-4)  /* an input or a step result is not finite */
+#define MCMP2_ETIMEOUT (-5)    /* a bounded device wait ran out */
+#define MCMP2_ENOSPACE (-6)    /* workspace or caller buffer too small */
+#define MCMP2_EUNSUPPORTED (-7) /* no sm_103 device, or a feature this build lacks */
+
+/* Arithmetic of the propagator and spinor contractions. */
+#define MCMP2_FP64 0   /* complex128 throughout (CUDA-core DFMA) */
+#define MCMP2_MIXED 1  /* split-BF16 x3 tensor-core products, FP32 accumulate; FP64 sampling and sums */
+
+/* Sampling constants (Sec. III leaves them open; see the library design notes). */
+#define MCMP2_DELTA0 0.6        /* initial Metropolis displacement (bohr) */
+#define MCMP2_ADAPT_WINDOW 20   /* burn-in steps per displacement adaptation */
+#define MCMP2_BLOCK_SIZE 100    /* Flyvbjerg-Petersen block size N_b (Sec. IV) */
+
+typedef struct mcmp2_ctx mcmp2_ctx;
+
+/* Problem sizes that fix the workspace. */
+typedef struct {
+    int n_centres;    /* atoms (centres of basis shells and of g) */
+    int n_functions;  /* n_L, scalar Cartesian Gaussians after shell expansion */
+    int n_occ;        /* occupied positive-energy spinors (even, >= 2) */
+    int n_vir;        /* virtual positive-energy spinors (even, >= 2) */
+    int m;            /* electron-pair walkers (>= 2) */
+    int n_tau;        /* imaginary times per step (>= 1) */
+} mcmp2_dims;
+
+/* Basis shells and the weight function g of Eq. basisSet. */
+typedef struct {
+    int n_centres;
+    const double *centres;      /* [n_centres][3] */
+    const double *weight;       /* [n_centres][4]: c1, zeta1, c2, zeta2 (Table 1 layout) */
+    int n_shells;
+    const int *shell_centre;    /* [n_shells] */
+    const int *shell_l;         /* [n_shells], 0..2 */
+    const double *shell_alpha;  /* [n_shells] exponents > 0 */
+    const double *shell_coef;   /* [n_shells] */
+} mcmp2_basis;
+
+/* Running statistics of the production steps (burn-in excluded). */
+typedef struct {
+    double energy;       /* I_N: mean of the complete block means */
+    double variance;     /* sigma_N^2 of Eq. uncertainty */
+    double error;        /* sigma-bar_N = sigma_N / sqrt(N/N_b) */
+    int64_t n_blocks;    /* complete blocks */
+    int64_t steps;       /* production steps accumulated */
+    double mean_all;     /* mean of all step estimates, incomplete block included */
+    double last_step;    /* I'_n of the latest step */
+    double accept_rate;  /* Metropolis acceptance over the production steps */
+} mcmp2_result;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL for the legacy default stream) in `precision`
+ * (MCMP2_FP64 or MCMP2_MIXED).  Fails with MCMP2_EUNSUPPORTED on devices
+ * other than compute capability 10.3. */
+int mcmp2_create(mcmp2_ctx **ctx, int device, void *cuda_stream, int precision);
+
+/* Release the context (not the caller's workspace).  NULL is ignored. */
+void mcmp2_destroy(mcmp2_ctx *ctx);
+
+/* Message of the last failed call on ctx (never NULL; "" if none). */
+const char *mcmp2_last_error(const mcmp2_ctx *ctx);
+
+/* Bytes of device workspace needed for `dims` in `precision`. */
+int mcmp2_workspace_bytes(const mcmp2_dims *dims, int precision, size_t *bytes);
+
+/* Bind a device workspace (256-byte aligned, >= mcmp2_workspace_bytes) for `dims`.
+ * Rebinding discards the loaded system, walkers and statistics. */
+int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, size_t bytes);
+
+/* Load the system: basis shells and weight function, n_occ occupied then n_vir
+ * virtual spinors with coefficients C_host (complex, [4 n_L][n_occ + n_vir]
+ * row-major, rows L-alpha, L-beta, S-alpha, S-beta blocks) and energies
+ * eps_host ([n_occ + n_vir]).  Sizes must match the bound dims.  Requires
+ * max occupied eps < min virtual eps (lambda = 2 (eps_LUMO - eps_HOMO) > 0).
+ * Host arrays are copied; N_g is evaluated in closed form. */
+int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n_vir,
+                      const double *C_host, const double *eps_host);
+
+/* Set the m walker pairs from r_host ([m][2][3]) and run `burn_in` Metropolis
+ * steps with seed `seed` (steps numbered from 0), adapting the displacement
+ * every MCMP2_ADAPT_WINDOW steps by delta <- delta * clamp(a/0.5, 0.5, 2) with
+ * a the window's acceptance fraction.  Resets the statistics and the step
+ * counter to burn_in. */
+int mcmp2_set_walkers(mcmp2_ctx *ctx, const double *r_host, uint64_t seed, int64_t burn_in);
+
+/* Run n production steps with seed `seed`: Metropolis move, n_tau inverse-CDF
+ * times, the pair-of-pairs estimate I'_n and the blocking update, all on the
+ * device.  Steps continue the context's step counter, so consecutive calls
+ * with one seed equal one call.  Writes the running statistics to out_host
+ * (may be NULL; then nothing is copied back). */
+int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out_host);
+
+/* Replay mode: evaluate I'_n for n given samples without moving walkers or
+ * touching the statistics.  r_host: [n][m][2][3]; tau_host: [n][n_tau] (> 0);
+ * per_step_host: [n] output. */
+int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double *tau_host,
+                     double *per_step_host);
+
+/* Copy the current walker positions ([m][2][3]) and displacement to the host. */
+int mcmp2_get_walkers(mcmp2_ctx *ctx, double *r_host, double *delta_host);
+
+/* Per-tile partial sums of the latest step, for sampled checks at full size:
+ * out_host[t * n_tiles + k] = sum over the pairs (p < q) of tile k of
+ * Re f/(w w w) at time t, tiles of `tile_pairs` pairs per side enumerated
+ * row by row over the upper triangle (bp <= bq).  *n_tiles and *tile_pairs
+ * are written; capacity is the length of out_host in doubles. */
+int mcmp2_debug_partials(mcmp2_ctx *ctx, double *out_host, size_t capacity, int *n_tiles,
+                         int *tile_pairs);
+
+/* Launch counters and CUDA-event timing of the pair-of-pairs contraction
+ * kernel (the dominant kernel), measured on the context's stream. */
+typedef struct {
+    int64_t launches;       /* kernels this context launched since the last reset */
+    int64_t pair_launches;  /* launches of the pair-of-pairs contraction kernel */
+    double pair_ms;         /* summed event time of those launches (ms); 0 unless timing is on */
+} mcmp2_profile_counters;
+
+/* mode 0: read the counters (synchronises the stream when timing is on);
+ * mode 1: reset them and time every later contraction launch with events;
+ * mode 2: reset them and stop timing.  out may be NULL for modes 1 and 2. */
+int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out_host);
+
+/* Size of a checkpoint (walkers, displacement, step counter, statistics,
+ * system digest) and its serialisation into / restoration from a host
+ * buffer.  Restoring into a context with the same system and dims continues
+ * bit-identically. */
+int mcmp2_checkpoint_bytes(const mcmp2_ctx *ctx, size_t *bytes);
+int mcmp2_checkpoint(mcmp2_ctx *ctx, void *buf_host, size_t capacity);
+int mcmp2_restore(mcmp2_ctx *ctx, const void *buf_host, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCMP2_H */

@@ -1,0 +1,128 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcmp2 {
+
+// Pairs of walker pairs are processed in square tiles of TILE_PAIRS pairs per side.
+constexpr int TILE_PAIRS_F64 = 8;     // FP64 form: 64 x 64 complex position-component blocks
+constexpr int TILE_PAIRS_MIXED = 16;  // mixed form: 128 x 128 (one tcgen05 M = N = 128 tile)
+
+// Running statistics of the production steps (Eq. uncertainty), kept on the device.
+struct Stats {
+    double block_sum, block_comp;  // Kahan sum of the current block's step estimates
+    long long in_block;            // steps in the current block
+    long long n_blocks;            // complete blocks
+    double mean, m2;               // Welford mean and sum of squared deviations of block means
+    long long steps;               // production steps
+    double all_sum, all_comp;      // Kahan sum over all production steps
+    double last;                   // latest I'_n
+    unsigned long long accepted;   // accepted Metropolis moves over production steps
+};
+
+// Device view of the loaded system (pointers into the caller's workspace).
+struct DevSystem {
+    int n_centres, n_shells, n_l, n_occ, n_vir, n_orb, m, n_tau;
+    const double *centres;     // [n_centres][3]
+    const double *wcoef;       // [n_centres][4]: c1 N(zeta1), zeta1, c2 N(zeta2), zeta2
+    const int *shell_centre;   // [n_shells]
+    const double *shell_alpha; // [n_shells]
+    const double *shell_coef;  // [n_shells]
+    const int *fn_shell;       // [n_l] shell of each Cartesian function
+    const int *fn_pow;         // [n_l][3] Cartesian powers
+    const double *eps;         // [n_orb]
+    double eps_homo, eps_lumo, lambda, Ng;
+    const double *WL;          // FP64 large operand [n_l][2][n_orb][2] (L-alpha, L-beta; re, im)
+    const double *WS;          // FP64 small operand [3 n_l][2][n_orb][2] (S-alpha, S-beta)
+    const float *WLf, *WSf;    // FP32 copies for the mixed form
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): a counter-based generator.
+// Counter layout: {step_lo, step_hi, index, tag}; key = {seed_lo, seed_hi}.
+// tag 0/1: Metropolis move of walker pair `index`; tag 2: imaginary time `index`.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw4(uint64_t seed, uint64_t step, uint32_t index, uint32_t tag)
+{
+    return philox4x32_10(make_uint4((uint32_t)step, (uint32_t)(step >> 32), index, tag),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// (0, 1) from 32 bits: (x + 1/2) 2^-32, exact in double.
+__device__ __forceinline__ double u32_open(uint32_t x)
+{
+    return __dmul_rn(__dadd_rn((double)x, 0.5), 2.3283064365386963e-10);
+}
+
+// (0, 1] from 53 bits of two words.
+__device__ __forceinline__ double u53_half_open(uint32_t a, uint32_t b)
+{
+    const double v = __dadd_rn(__dadd_rn(__dmul_rn((double)(a >> 5), 67108864.0), (double)(b >> 6)), 1.0);
+    return __dmul_rn(v, 1.0 / 9007199254740992.0);
+}
+
+// Weight function g(r) of Eq. basisSet, with c N(zeta) folded on the host.
+// Every operation is rounded as written (no contraction) so that the walk is
+// reproducible from the same counters on any IEEE machine up to exp().
+__device__ __forceinline__ double weight_g(const DevSystem &s, double x, double y, double z)
+{
+    double g = 0.0;
+    for (int i = 0; i < s.n_centres; ++i) {
+        const double dx = __dsub_rn(x, s.centres[3 * i + 0]);
+        const double dy = __dsub_rn(y, s.centres[3 * i + 1]);
+        const double dz = __dsub_rn(z, s.centres[3 * i + 2]);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        const double *w = s.wcoef + 4 * i;
+        const double t1 = __dmul_rn(w[0], exp(__dmul_rn(-w[1], d2)));
+        const double t2 = __dmul_rn(w[2], exp(__dmul_rn(-w[3], d2)));
+        g = __dadd_rn(g, __dadd_rn(t1, t2));
+    }
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (defined in the kernel translation units).  All take the
+// context's stream and return cudaGetLastError() of the launch.
+// ---------------------------------------------------------------------------
+cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long long *step,
+                              uint64_t seed, double delta, unsigned long long *accepted,
+                              cudaStream_t st);
+cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, cudaStream_t st);
+cudaError_t launch_times(const DevSystem &s, const unsigned long long *step, uint64_t seed,
+                         const double *tau_given, double *tau, double *scale, cudaStream_t st);
+cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_basis(const DevSystem &s, const double *r, T *B, cudaStream_t st);
+
+cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi, cudaStream_t st);
+cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale,
+                             const double *a, double *partials, cudaStream_t st);
+
+cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tiles, double *out_slot,
+                          Stats *stats, int update_stats, unsigned long long *step_to_advance,
+                          cudaStream_t st);
+
+__host__ __device__ inline int pair_blocks(int m, int tile_pairs) { return (m + tile_pairs - 1) / tile_pairs; }
+__host__ __device__ inline int n_tiles_for(int m, int tile_pairs)
+{
+    const int nb = pair_blocks(m, tile_pairs);
+    return nb * (nb + 1) / 2;
+}
+
+}  // namespace mcmp2

@@ -1,0 +1,324 @@
+// FP64 form of the integrand engine: basis values at the walker positions,
+// spinor formation (Eq. C with kinetic balance) and the propagator blocks with
+// the traced direct and exchange products (trace form of Eq. MCMP2).
+// GB300 runs FP64 on CUDA cores only, so these kernels are plain DFMA code;
+// the mixed form (k_mixed.cu) is the tensor-core path.
+#include "internal.cuh"
+
+namespace mcmp2 {
+
+// ---------------------------------------------------------------------------
+// Basis values: B[x][0:n_l] = g_mu(r_x), B[x][(1+j) n_l + mu] = d g_mu / d x_j.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void basis_kernel(DevSystem s, const double *__restrict__ r, T *__restrict__ B, int ldb)
+{
+    const int x = blockIdx.y;
+    const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mu >= s.n_l) return;
+    const int sh = s.fn_shell[mu];
+    const double *A = s.centres + 3 * s.shell_centre[sh];
+    const double d[3] = {r[3 * x + 0] - A[0], r[3 * x + 1] - A[1], r[3 * x + 2] - A[2]};
+    const double al = s.shell_alpha[sh];
+    const double e = s.shell_coef[sh] * exp(-al * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    const int pw[3] = {s.fn_pow[3 * mu], s.fn_pow[3 * mu + 1], s.fn_pow[3 * mu + 2]};
+    double pk[3], dk[3];  // x_j^a and d/dx_j [x_j^a e^{-al x_j^2}] / e^{-al x_j^2}
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double v = 1.0;
+        for (int i = 0; i < pw[j]; ++i) v *= d[j];
+        pk[j] = v;
+        double lower = 0.0;
+        if (pw[j] > 0) {
+            lower = 1.0;
+            for (int i = 0; i < pw[j] - 1; ++i) lower *= d[j];
+            lower *= pw[j];
+        }
+        dk[j] = lower - 2.0 * al * v * d[j];
+    }
+    T *row = B + (size_t)x * ldb;
+    row[mu] = (T)(pk[0] * pk[1] * pk[2] * e);
+    row[s.n_l + mu] = (T)(dk[0] * pk[1] * pk[2] * e);
+    row[2 * s.n_l + mu] = (T)(pk[0] * dk[1] * pk[2] * e);
+    row[3 * s.n_l + mu] = (T)(pk[0] * pk[1] * dk[2] * e);
+}
+
+template <typename T>
+cudaError_t launch_basis(const DevSystem &s, const double *r, T *B, cudaStream_t st)
+{
+    const int threads = 128;
+    dim3 grid((s.n_l + threads - 1) / threads, 2 * s.m);
+    basis_kernel<T><<<grid, threads, 0, st>>>(s, r, B, 4 * s.n_l);
+    return cudaGetLastError();
+}
+template cudaError_t launch_basis<double>(const DevSystem &, const double *, double *, cudaStream_t);
+template cudaError_t launch_basis<float>(const DevSystem &, const double *, float *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Row-major C[M x N] = A[M x K] B[K x N]: 64 x 64 tiles, 4 x 4 per thread.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_rm_kernel(int M, int N, int K, const T *__restrict__ A, int lda,
+                                                      const T *__restrict__ Bm, int ldb, T *__restrict__ C,
+                                                      int ldc)
+{
+    __shared__ T As[16][64 + 1];
+    __shared__ T Bs[16][64 + 1];
+    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+            const int rr = i >> 4, kk = i & 15;
+            const int gr = row0 + rr, gk = k0 + kk;
+            As[kk][rr] = (gr < M && gk < K) ? A[(size_t)gr * lda + gk] : T(0);
+            const int kb = i >> 6, cc = i & 63;
+            const int gkb = k0 + kb, gc = col0 + cc;
+            Bs[kb][cc] = (gkb < K && gc < N) ? Bm[(size_t)gkb * ldb + gc] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gr = row0 + ty + 16 * i, gc = col0 + tx + 16 * j;
+            if (gr < M && gc < N) C[(size_t)gr * ldc + gc] = acc[i][j];
+        }
+}
+
+template <typename T>
+static cudaError_t gemm_rm(int M, int N, int K, const T *A, int lda, const T *B, int ldb, T *C, int ldc,
+                           cudaStream_t st)
+{
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    gemm_rm_kernel<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    return cudaGetLastError();
+}
+
+// Spinor values phi[x][c][k] (complex, c = L-alpha, L-beta, S-alpha, S-beta):
+// the large components contract basis values with C^L (Eq. C); the small ones
+// contract the gradients with the Pauli-folded C^S (Eq. KB).
+cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi, cudaStream_t st)
+{
+    const int P = 2 * s.m, n4 = 4 * s.n_orb, ld = 8 * s.n_orb;
+    cudaError_t e = gemm_rm<double>(P, n4, s.n_l, B, 4 * s.n_l, s.WL, n4, phi, ld, st);
+    if (e != cudaSuccess) return e;
+    return gemm_rm<double>(P, n4, 3 * s.n_l, B + s.n_l, 4 * s.n_l, s.WS, n4, phi + n4, ld, st);
+}
+
+cudaError_t launch_spinors_f32(const DevSystem &s, const float *B, float *phi, cudaStream_t st)
+{
+    const int P = 2 * s.m, n4 = 4 * s.n_orb, ld = 8 * s.n_orb;
+    cudaError_t e = gemm_rm<float>(P, n4, s.n_l, B, 4 * s.n_l, s.WLf, n4, phi, ld, st);
+    if (e != cudaSuccess) return e;
+    return gemm_rm<float>(P, n4, 3 * s.n_l, B + s.n_l, 4 * s.n_l, s.WSf, n4, phi + n4, ld, st);
+}
+
+// ---------------------------------------------------------------------------
+// Pair-of-pairs tiles (FP64 form)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tile_coords(int tile, int nb, int &bp, int &bq)
+{
+    int k = tile, b = 0;
+    while (k >= nb - b) {
+        k -= nb - b;
+        ++b;
+    }
+    bp = b;
+    bq = b + k;
+}
+
+constexpr int F64_TP = TILE_PAIRS_F64;  // 8 pairs = 16 positions = 64 rows per side
+constexpr int F64_KC = 16;              // orbitals per staged chunk
+
+struct F64Smem {
+    double2 Gm[2][F64_TP][F64_TP][16];  // G-(x, y) for same-electron position pairs, [e][xp][yp][c*4+d]
+    union {
+        struct {
+            double2 A[F64_KC][64];
+            double2 B[F64_KC][64];
+        } ld;
+        double2 Gp[16][16][16];          // G+(x, y) for all position pairs, [xl][yl][c*4+d]
+    } u;
+    double part[64];
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b)  // conj(a) * b
+{
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// One CTA per (tile, tau).  Rows of a tile side are (position, component)
+// = 4 x_local + c with x_local = 2 p_local + e.  Threads 0..127 own the
+// same-electron position blocks (G- and G+), threads 128..255 the cross ones
+// (G+ only, since the trace form uses G- only between like electrons).
+__global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const double2 *__restrict__ phi,
+                                                           const double *__restrict__ scale,
+                                                           const double *__restrict__ a,
+                                                           double *__restrict__ partials, int n_tiles)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F64Smem &sm = *reinterpret_cast<F64Smem *>(smem_raw);
+    const int tile = blockIdx.x, t = blockIdx.y;
+    const int nb = pair_blocks(s.m, F64_TP);
+    int bp, bq;
+    tile_coords(tile, nb, bp, bq);
+    const int tid = threadIdx.x;
+    const int half = tid >> 7, e = (tid >> 6) & 1, i = tid & 63;
+    const int xp = i >> 3, yp = i & 7;
+    const int xl = 2 * xp + e, yl = 2 * yp + (half ? 1 - e : e);
+    const double *sc = scale + (size_t)t * s.n_orb;
+    const int row_base_p = 8 * F64_TP * bp, row_base_q = 8 * F64_TP * bq;
+    const int rows_valid = 8 * s.m;
+
+    double2 acc[16];
+    for (int pass = 0; pass < 2; ++pass) {  // 0: occupied (G-), 1: virtual (G+)
+        const int k_begin = pass == 0 ? 0 : s.n_occ;
+        const int k_end = pass == 0 ? s.n_occ : s.n_orb;
+        const bool active = (pass == 1) || (half == 0);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = make_double2(0.0, 0.0);
+        for (int k0 = k_begin; k0 < k_end; k0 += F64_KC) {
+            for (int idx = tid; idx < F64_KC * 64; idx += 256) {
+                const int row = idx >> 4, kk = idx & 15, k = k0 + kk;
+                double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
+                if (k < k_end) {
+                    const double f = sc[k];
+                    const int ra = row_base_p + row, rb = row_base_q + row;
+                    if (ra < rows_valid) {
+                        va = phi[(size_t)ra * s.n_orb + k];
+                        va.x *= f;
+                        va.y *= f;
+                    }
+                    if (rb < rows_valid) {
+                        vb = phi[(size_t)rb * s.n_orb + k];
+                        vb.x *= f;
+                        vb.y *= f;
+                    }
+                }
+                sm.u.ld.A[kk][row] = va;
+                sm.u.ld.B[kk][row] = vb;
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll 4
+                for (int kk = 0; kk < F64_KC; ++kk) {
+                    double2 xa[4], yb[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) xa[c] = sm.u.ld.A[kk][4 * xl + c];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) yb[d] = sm.u.ld.B[kk][4 * yl + d];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) {
+                            // G(x, y)_cd += X(x)_c conj(X(y)_d)
+                            double2 &g = acc[4 * c + d];
+                            g.x = fma(xa[c].x, yb[d].x, g.x);
+                            g.x = fma(xa[c].y, yb[d].y, g.x);
+                            g.y = fma(xa[c].y, yb[d].x, g.y);
+                            g.y = fma(-xa[c].x, yb[d].y, g.y);
+                        }
+                }
+            }
+            __syncthreads();
+        }
+        if (pass == 0 && half == 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sm.Gm[e][xp][yp][j] = acc[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sm.u.Gp[xl][yl][j] = acc[j];
+    __syncthreads();
+
+    // Epilogue: one thread per pair of pairs (p, q) of the tile.
+    if (tid < 64) {
+        const int px = tid >> 3, qy = tid & 7;
+        const int p = F64_TP * bp + px, q = F64_TP * bq + qy;
+        double v = 0.0;
+        if (p < s.m && q < s.m && (bp < bq || px < qy)) {
+            const double2 *M1 = sm.Gm[0][px][qy];          // G-(1p, 1q)
+            const double2 *M3 = sm.Gm[1][px][qy];          // G-(2p, 2q)
+            const double2 *N11 = sm.u.Gp[2 * px][2 * qy];  // G+(1p, 1q)
+            const double2 *N22 = sm.u.Gp[2 * px + 1][2 * qy + 1];  // G+(2p, 2q)
+            const double2 *M2 = sm.u.Gp[2 * px][2 * qy + 1];  // G+(1p, 2q)
+            const double2 *M4 = sm.u.Gp[2 * px + 1][2 * qy];  // G+(2p, 1q)
+            // Direct: tr[G-(1q,1p) G+(1p,1q)] tr[G-(2q,2p) G+(2p,2q)], G-(y,x) = G-(x,y)^dagger.
+            double2 t1 = make_double2(0, 0), t2 = make_double2(0, 0);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const double2 u1 = cmulc(M1[j], N11[j]), u2 = cmulc(M3[j], N22[j]);
+                t1.x += u1.x;
+                t1.y += u1.y;
+                t2.x += u2.x;
+                t2.y += u2.y;
+            }
+            const double2 direct = cmul(t1, t2);
+            // Exchange: tr[G-(1q,1p) G+(1p,2q) G-(2q,2p) G+(2p,1q)] = tr[(M1^dag M2)(M3^dag M4)]
+            // = sum_ij (M1^dag M2)_ij (M3^dag M4)_ji.
+            double2 ex = make_double2(0, 0);
+#pragma unroll
+            for (int i2 = 0; i2 < 4; ++i2)
+#pragma unroll
+                for (int j2 = 0; j2 < 4; ++j2) {
+                    double2 s1 = make_double2(0, 0), s2 = make_double2(0, 0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const double2 w1 = cmulc(M1[4 * k + i2], M2[4 * k + j2]);
+                        const double2 w2 = cmulc(M3[4 * k + j2], M4[4 * k + i2]);
+                        s1.x += w1.x;
+                        s1.y += w1.y;
+                        s2.x += w2.x;
+                        s2.y += w2.y;
+                    }
+                    const double2 w = cmul(s1, s2);
+                    ex.x += w.x;
+                    ex.y += w.y;
+                }
+            const double F = -0.5 * (direct.x - ex.x);  // real part of -1/2 (direct - exchange)
+            v = F * a[p] * a[q] / s.lambda;
+        }
+        sm.part[tid] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int j = 0; j < 64; ++j) sum += sm.part[j];
+        partials[(size_t)t * n_tiles + tile] = sum;
+    }
+}
+
+cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale, const double *a,
+                             double *partials, cudaStream_t st)
+{
+    static bool configured = false;
+    const size_t smem = sizeof(F64Smem);
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(pairs_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int n_tiles = n_tiles_for(s.m, F64_TP);
+    dim3 grid(n_tiles, s.n_tau);
+    pairs_f64_kernel<<<grid, 256, smem, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, a, partials,
+                                              n_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace mcmp2

@@ -1,0 +1,128 @@
+// Sampling kernels: Metropolis walk of the electron pairs (Sec. III, Metropolis
+// sampling of w(r1,r2)), the per-pair weight factors, and the inverse-CDF
+// imaginary times with the per-orbital propagator scales.
+#include "internal.cuh"
+
+namespace mcmp2 {
+
+// One Metropolis step for every walker pair: both electrons move by a uniform
+// displacement in [-delta, delta]^3; the move is accepted with probability
+// min(1, w'/w) with w = g(r1) g(r2) / r12 (the 1/N_g cancels).  FP64 with
+// explicit rounding so the same counters give the same walk on the host.
+__global__ void metropolis_kernel(DevSystem s, double *__restrict__ r,
+                                  const unsigned long long *__restrict__ step_ptr, uint64_t seed,
+                                  double delta, unsigned long long *__restrict__ accepted)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int acc = 0;
+    if (p < s.m) {
+        const uint64_t step = *step_ptr;
+        const uint4 a = draw4(seed, step, (uint32_t)p, 0u);
+        const uint4 b = draw4(seed, step, (uint32_t)p, 1u);
+        const uint32_t u[7] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+        double *r1 = r + 6 * p, *r2 = r1 + 3;
+        double o1[3], o2[3], n1[3], n2[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            o1[j] = r1[j];
+            o2[j] = r2[j];
+            n1[j] = __dadd_rn(o1[j], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[j])), 1.0)));
+            n2[j] = __dadd_rn(o2[j], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[3 + j])), 1.0)));
+        }
+        auto pair_w = [&](const double *x1, const double *x2) {
+            const double dx = __dsub_rn(x1[0], x2[0]), dy = __dsub_rn(x1[1], x2[1]), dz = __dsub_rn(x1[2], x2[2]);
+            const double r12 = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+            return __ddiv_rn(__dmul_rn(weight_g(s, x1[0], x1[1], x1[2]), weight_g(s, x2[0], x2[1], x2[2])), r12);
+        };
+        const double w_old = pair_w(o1, o2);
+        const double w_new = pair_w(n1, n2);
+        if (__dmul_rn(u32_open(u[6]), w_old) < w_new) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                r1[j] = n1[j];
+                r2[j] = n2[j];
+            }
+            acc = 1;
+        }
+    }
+    // One atomic per warp.
+    const unsigned int total = __reduce_add_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && total) atomicAdd(accepted, (unsigned long long)total);
+}
+
+// a_p = N_g / (g(r1p) g(r2p)): with 1/(w w) this is the weight factor of a pair of pairs.
+__global__ void pair_weights_kernel(DevSystem s, const double *__restrict__ r, double *__restrict__ a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.m) return;
+    const double *r1 = r + 6 * p, *r2 = r1 + 3;
+    const double g1 = weight_g(s, r1[0], r1[1], r1[2]);
+    const double g2 = weight_g(s, r2[0], r2[1], r2[2]);
+    a[p] = s.Ng / (g1 * g2);
+}
+
+// Imaginary times and propagator scales for one step.  Block t handles time t:
+// tau_t = -ln(u)/lambda (analytic inverse CDF of Eq. tauWeight) unless given,
+// then scale[t][i] = exp((eps_i - eps_HOMO) tau/2) for occupied and
+// scale[t][a] = exp(-(eps_a - eps_LUMO) tau/2) for virtual spinors, so that a
+// product X X^dagger of scaled spinor values carries exp(+eps_i tau) or
+// exp(-eps_a tau) times exp(-eps_HOMO tau) or exp(+eps_LUMO tau); every factor
+// is at most 1 and the four shifts of a pair of pairs multiply to exp(lambda tau).
+__global__ void times_kernel(DevSystem s, const unsigned long long *__restrict__ step_ptr, uint64_t seed,
+                             const double *__restrict__ tau_given, double *__restrict__ tau,
+                             double *__restrict__ scale)
+{
+    const int t = blockIdx.x;
+    __shared__ double tt;
+    if (threadIdx.x == 0) {
+        double v;
+        if (tau_given) {
+            v = tau_given[t];
+        } else {
+            const uint4 o = draw4(seed, *step_ptr, (uint32_t)t, 2u);
+            v = -log(u53_half_open(o.x, o.y)) / s.lambda;
+        }
+        tt = v;
+        tau[t] = v;
+    }
+    __syncthreads();
+    const double x = tt;
+    for (int k = threadIdx.x; k < s.n_orb; k += blockDim.x) {
+        const double e = s.eps[k];
+        const double arg = (k < s.n_occ) ? (e - s.eps_homo) : -(e - s.eps_lumo);
+        scale[(size_t)t * s.n_orb + k] = exp(0.5 * arg * x);
+    }
+}
+
+__global__ void advance_step_kernel(unsigned long long *step) { *step += 1ull; }
+
+cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long long *step,
+                              uint64_t seed, double delta, unsigned long long *accepted,
+                              cudaStream_t st)
+{
+    const int threads = 128;
+    metropolis_kernel<<<(s.m + threads - 1) / threads, threads, 0, st>>>(s, r, step, seed, delta, accepted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, cudaStream_t st)
+{
+    const int threads = 128;
+    pair_weights_kernel<<<(s.m + threads - 1) / threads, threads, 0, st>>>(s, r, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_times(const DevSystem &s, const unsigned long long *step, uint64_t seed,
+                         const double *tau_given, double *tau, double *scale, cudaStream_t st)
+{
+    times_kernel<<<s.n_tau, 256, 0, st>>>(s, step, seed, tau_given, tau, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t st)
+{
+    advance_step_kernel<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError();
+}
+
+}  // namespace mcmp2

@@ -1,0 +1,698 @@
+// C ABI of the library (include/mcmp2.h): context, caller-owned workspace,
+// system loading with the host-side folding of the spinor coefficients, and
+// the orchestration of sampling, integrand and statistics on one stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mcmp2.h"
+#include "internal.cuh"
+#include "mixed.cuh"
+
+using namespace mcmp2;
+
+namespace {
+
+constexpr int REPLAY_CHUNK = 16;  // replay-mode steps staged per host->device copy
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Offsets of every array inside the caller's workspace.
+struct Layout {
+    size_t centres, wcoef, shell_centre, shell_alpha, shell_coef, fn_shell, fn_pow, eps, WL, WS, WLf, WSf;
+    size_t r, a, tau, scale, step, burn_acc, stats, per_step, stage_r, stage_tau;
+    size_t B, phi, partials;
+    MixedLayout mixed;
+    size_t total;
+    int tile_pairs, n_tiles;
+};
+
+bool dims_valid(const mcmp2_dims *d)
+{
+    return d && d->n_centres >= 1 && d->n_functions >= 1 && d->n_occ >= 2 && d->n_vir >= 2 && d->m >= 2 &&
+           d->n_tau >= 1 && d->n_occ % 2 == 0 && d->n_vir % 2 == 0 && d->n_functions <= 65536 &&
+           d->m <= (1 << 20) && d->n_tau <= 64 && d->n_occ + d->n_vir <= 65536;
+}
+
+Layout make_layout(const mcmp2_dims &d, int precision)
+{
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t nl = d.n_functions, no = d.n_occ + d.n_vir, m = d.m, nc = d.n_centres;
+    L.centres = take(nc * 3 * 8);
+    L.wcoef = take(nc * 4 * 8);
+    L.shell_centre = take(nl * 4);
+    L.shell_alpha = take(nl * 8);
+    L.shell_coef = take(nl * 8);
+    L.fn_shell = take(nl * 4);
+    L.fn_pow = take(nl * 3 * 4);
+    L.eps = take(no * 8);
+    L.WL = take(nl * 4 * no * 8);
+    L.WS = take(3 * nl * 4 * no * 8);
+    L.r = take(m * 6 * 8);
+    L.a = take(m * 8);
+    L.tau = take(d.n_tau * 8);
+    L.scale = take(d.n_tau * no * 8);
+    L.step = take(8);
+    L.burn_acc = take(8);
+    L.stats = take(sizeof(Stats));
+    L.per_step = take(REPLAY_CHUNK * 8);
+    L.stage_r = take(REPLAY_CHUNK * m * 6 * 8);
+    L.stage_tau = take(REPLAY_CHUNK * d.n_tau * 8);
+    if (precision == MCMP2_FP64) {
+        L.tile_pairs = TILE_PAIRS_F64;
+        L.B = take(2 * m * 4 * nl * 8);
+        L.phi = take(8 * m * no * 16);
+    } else {
+        L.tile_pairs = TILE_PAIRS_MIXED;
+        L.WLf = take(nl * 4 * no * 4);
+        L.WSf = take(3 * nl * 4 * no * 4);
+        L.B = take(2 * m * 4 * nl * 4);
+        L.phi = take(8 * m * no * 8);
+        L.mixed = mixed_layout(d.m, d.n_occ, d.n_vir, off);
+        off = align256(L.mixed.end);
+    }
+    L.n_tiles = n_tiles_for(d.m, L.tile_pairs);
+    L.partials = take((size_t)d.n_tau * L.n_tiles * 8);
+    L.total = off;
+    return L;
+}
+
+uint64_t fnv1a(uint64_t h, const void *data, size_t n)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+const int NCART[3] = {1, 3, 6};
+const int CART[3][6][3] = {
+    {{0, 0, 0}},
+    {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},
+    {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}},
+};
+
+struct Checkpoint {
+    uint64_t magic, version;
+    mcmp2_dims dims;
+    uint64_t digest;
+    unsigned long long step;
+    double delta;
+    Stats stats;
+};
+constexpr uint64_t CK_MAGIC = 0x324d43504d32434dull;  // "MC2PMC2M"
+
+}  // namespace
+
+struct mcmp2_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int precision = MCMP2_FP64;
+    std::string err;
+    bool bound = false, loaded = false, walkers = false;
+    mcmp2_dims dims{};
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L{};
+    DevSystem sys{};
+    double delta = MCMP2_DELTA0;
+    uint64_t digest = 0;
+    MixedPlan mixed{};
+    // profiling
+    long long launches = 0, pair_launches = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pair_events;
+
+    int fail(int code, const char *fmt, ...)
+    {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda(cudaError_t e, const char *what)
+    {
+        if (e == cudaSuccess) return MCMP2_OK;
+        return fail(MCMP2_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+    template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(ws + off); }
+};
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        const int rc_ = ctx->cuda((call), (what));       \
+        if (rc_ != MCMP2_OK) return rc_;                 \
+    } while (0)
+
+extern "C" {
+
+int mcmp2_create(mcmp2_ctx **out, int device, void *cuda_stream, int precision)
+{
+    if (!out) return MCMP2_EINVAL;
+    *out = nullptr;
+    if (precision != MCMP2_FP64 && precision != MCMP2_MIXED) return MCMP2_EINVAL;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return MCMP2_EUNSUPPORTED;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MCMP2_ECUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return MCMP2_EUNSUPPORTED;
+    auto *ctx = new mcmp2_ctx();
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx->precision = precision;
+    *out = ctx;
+    return MCMP2_OK;
+}
+
+static void drop_events(mcmp2_ctx *ctx)
+{
+    for (auto &ev : ctx->pair_events) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    ctx->pair_events.clear();
+}
+
+void mcmp2_destroy(mcmp2_ctx *ctx)
+{
+    if (!ctx) return;
+    drop_events(ctx);
+    mixed_release(ctx->mixed);
+    delete ctx;
+}
+
+const char *mcmp2_last_error(const mcmp2_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int mcmp2_workspace_bytes(const mcmp2_dims *dims, int precision, size_t *bytes)
+{
+    if (!dims_valid(dims) || !bytes || (precision != MCMP2_FP64 && precision != MCMP2_MIXED))
+        return MCMP2_EINVAL;
+    *bytes = make_layout(*dims, precision).total;
+    return MCMP2_OK;
+}
+
+int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, size_t bytes)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!dims_valid(dims)) return ctx->fail(MCMP2_EINVAL, "invalid dims");
+    if (!dptr || (reinterpret_cast<uintptr_t>(dptr) & 255)) return ctx->fail(MCMP2_EINVAL, "workspace must be 256-byte aligned");
+    const Layout L = make_layout(*dims, ctx->precision);
+    if (bytes < L.total) return ctx->fail(MCMP2_ENOSPACE, "workspace %zu bytes < %zu needed", bytes, L.total);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->dims = *dims;
+    ctx->L = L;
+    ctx->ws = static_cast<char *>(dptr);
+    ctx->ws_bytes = bytes;
+    ctx->bound = true;
+    ctx->loaded = ctx->walkers = false;
+    return MCMP2_OK;
+}
+
+int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir, const double *C,
+                      const double *eps)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->bound) return ctx->fail(MCMP2_ENOTLOADED, "no workspace bound");
+    const mcmp2_dims &d = ctx->dims;
+    if (!b || !C || !eps || !b->centres || !b->weight || !b->shell_centre || !b->shell_l || !b->shell_alpha ||
+        !b->shell_coef)
+        return ctx->fail(MCMP2_EINVAL, "null pointer in system");
+    if (b->n_centres != d.n_centres || n_occ != d.n_occ || n_vir != d.n_vir || b->n_shells < 1)
+        return ctx->fail(MCMP2_EINVAL, "system sizes do not match the bound dims");
+    // Expand shells to Cartesian functions.
+    std::vector<int> fn_shell, fn_pow;
+    for (int k = 0; k < b->n_shells; ++k) {
+        const int l = b->shell_l[k];
+        if (l < 0 || l > 2) return ctx->fail(MCMP2_EINVAL, "shell %d: l=%d not in 0..2", k, l);
+        if (b->shell_centre[k] < 0 || b->shell_centre[k] >= b->n_centres)
+            return ctx->fail(MCMP2_EINVAL, "shell %d: bad centre", k);
+        if (!(b->shell_alpha[k] > 0.0) || !std::isfinite(b->shell_alpha[k]) || !std::isfinite(b->shell_coef[k]))
+            return ctx->fail(MCMP2_EINVAL, "shell %d: bad exponent or coefficient", k);
+        for (int c = 0; c < NCART[l]; ++c) {
+            fn_shell.push_back(k);
+            for (int j = 0; j < 3; ++j) fn_pow.push_back(CART[l][c][j]);
+        }
+    }
+    const int nl = (int)fn_shell.size();
+    if (nl != d.n_functions) return ctx->fail(MCMP2_EINVAL, "basis has %d functions, dims say %d", nl, d.n_functions);
+    if (b->n_shells > nl) return ctx->fail(MCMP2_EINVAL, "too many shells");
+    const int no = n_occ + n_vir;
+    for (size_t i = 0; i < (size_t)4 * nl * no * 2; ++i)
+        if (!std::isfinite(C[i])) return ctx->fail(MCMP2_ENONFINITE, "C has a non-finite entry");
+    double homo = -INFINITY, lumo = INFINITY;
+    for (int k = 0; k < no; ++k) {
+        if (!std::isfinite(eps[k])) return ctx->fail(MCMP2_ENONFINITE, "eps has a non-finite entry");
+        if (k < n_occ) homo = std::fmax(homo, eps[k]);
+        else lumo = std::fmin(lumo, eps[k]);
+    }
+    if (!(lumo > homo)) return ctx->fail(MCMP2_EINVAL, "need max occupied eps < min virtual eps");
+    for (int i = 0; i < b->n_centres; ++i) {
+        for (int j = 0; j < 3; ++j)
+            if (!std::isfinite(b->centres[3 * i + j])) return ctx->fail(MCMP2_ENONFINITE, "bad centre");
+        if (!(b->weight[4 * i + 1] > 0.0) || !(b->weight[4 * i + 3] > 0.0) || !std::isfinite(b->weight[4 * i]) ||
+            !std::isfinite(b->weight[4 * i + 2]))
+            return ctx->fail(MCMP2_EINVAL, "centre %d: bad weight parameters", i);
+    }
+    // Weight function: c N(zeta) with N(zeta) = (2 zeta / pi)^{3/4} (Eq. basisSet).
+    std::vector<double> wcoef(4 * (size_t)b->n_centres);
+    for (int i = 0; i < b->n_centres; ++i) {
+        const double *w = b->weight + 4 * i;
+        wcoef[4 * i + 0] = w[0] * std::pow(2.0 * w[1] / M_PI, 0.75);
+        wcoef[4 * i + 1] = w[1];
+        wcoef[4 * i + 2] = w[2] * std::pow(2.0 * w[3] / M_PI, 0.75);
+        wcoef[4 * i + 3] = w[3];
+    }
+    // N_g = Int Int g g / r12 in closed form: each pair of s Gaussians exp(-a r_A^2),
+    // exp(-b r_B^2) contributes (pi/a)^{3/2} (pi/b)^{3/2} erf(sqrt(ab/(a+b)) R)/R.
+    double Ng = 0.0;
+    for (int i = 0; i < b->n_centres; ++i)
+        for (int j = 0; j < b->n_centres; ++j) {
+            const double *A = b->centres + 3 * i, *B = b->centres + 3 * j;
+            const double R = std::sqrt((A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) +
+                                       (A[2] - B[2]) * (A[2] - B[2]));
+            for (int u = 0; u < 2; ++u)
+                for (int v = 0; v < 2; ++v) {
+                    const double ca = wcoef[4 * i + 2 * u], za = wcoef[4 * i + 2 * u + 1];
+                    const double cb = wcoef[4 * j + 2 * v], zb = wcoef[4 * j + 2 * v + 1];
+                    const double rho = za * zb / (za + zb);
+                    const double f = R > 0.0 ? std::erf(std::sqrt(rho) * R) / R : 2.0 * std::sqrt(rho / M_PI);
+                    Ng += ca * cb * std::pow(M_PI / za, 1.5) * std::pow(M_PI / zb, 1.5) * f;
+                }
+        }
+    // Spinor-formation operands.  Large: WL[mu][c][k] = C^{L c}_{mu k}.  Small:
+    // phi^S = sum_mu sum_s C^{S s}_{mu k} (sigma.grad)(g_mu e_s), so the
+    // gradient component j of g_mu enters component c' with sigma_j[c'][s] C^{S s}.
+    const double sig_re[3][2][2] = {{{0, 1}, {1, 0}}, {{0, 0}, {0, 0}}, {{1, 0}, {0, -1}}};
+    const double sig_im[3][2][2] = {{{0, 0}, {0, 0}}, {{0, -1}, {1, 0}}, {{0, 0}, {0, 0}}};
+    std::vector<double> WL((size_t)nl * 4 * no), WS((size_t)3 * nl * 4 * no);
+    auto Cre = [&](int row, int k) { return C[((size_t)row * no + k) * 2]; };
+    auto Cim = [&](int row, int k) { return C[((size_t)row * no + k) * 2 + 1]; };
+    for (int mu = 0; mu < nl; ++mu)
+        for (int c = 0; c < 2; ++c)
+            for (int k = 0; k < no; ++k) {
+                WL[(((size_t)mu * 2 + c) * no + k) * 2 + 0] = Cre(c * nl + mu, k);
+                WL[(((size_t)mu * 2 + c) * no + k) * 2 + 1] = Cim(c * nl + mu, k);
+            }
+    for (int j = 0; j < 3; ++j)
+        for (int mu = 0; mu < nl; ++mu)
+            for (int cp = 0; cp < 2; ++cp)
+                for (int k = 0; k < no; ++k) {
+                    double re = 0.0, im = 0.0;
+                    for (int s = 0; s < 2; ++s) {
+                        const double sr = sig_re[j][cp][s], si = sig_im[j][cp][s];
+                        const double cr = Cre((2 + s) * nl + mu, k), ci = Cim((2 + s) * nl + mu, k);
+                        re += sr * cr - si * ci;
+                        im += sr * ci + si * cr;
+                    }
+                    const size_t o = ((((size_t)j * nl + mu) * 2 + cp) * no + k) * 2;
+                    WS[o] = re;
+                    WS[o + 1] = im;
+                }
+    std::vector<double> shell_alpha(b->shell_alpha, b->shell_alpha + b->n_shells);
+    std::vector<double> shell_coef(b->shell_coef, b->shell_coef + b->n_shells);
+    std::vector<int> shell_centre(b->shell_centre, b->shell_centre + b->n_shells);
+
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const Layout &L = ctx->L;
+    cudaStream_t st = ctx->stream;
+    auto h2d = [&](size_t off, const void *src, size_t n) {
+        return cudaMemcpyAsync(ctx->ws + off, src, n, cudaMemcpyHostToDevice, st);
+    };
+    CK(h2d(L.centres, b->centres, sizeof(double) * 3 * b->n_centres), "copy centres");
+    CK(h2d(L.wcoef, wcoef.data(), sizeof(double) * wcoef.size()), "copy weights");
+    CK(h2d(L.shell_centre, shell_centre.data(), sizeof(int) * shell_centre.size()), "copy shells");
+    CK(h2d(L.shell_alpha, shell_alpha.data(), sizeof(double) * shell_alpha.size()), "copy shells");
+    CK(h2d(L.shell_coef, shell_coef.data(), sizeof(double) * shell_coef.size()), "copy shells");
+    CK(h2d(L.fn_shell, fn_shell.data(), sizeof(int) * fn_shell.size()), "copy functions");
+    CK(h2d(L.fn_pow, fn_pow.data(), sizeof(int) * fn_pow.size()), "copy functions");
+    CK(h2d(L.eps, eps, sizeof(double) * no), "copy eps");
+    CK(h2d(L.WL, WL.data(), sizeof(double) * WL.size()), "copy WL");
+    CK(h2d(L.WS, WS.data(), sizeof(double) * WS.size()), "copy WS");
+    if (ctx->precision == MCMP2_MIXED) {
+        std::vector<float> WLf(WL.begin(), WL.end()), WSf(WS.begin(), WS.end());
+        CK(h2d(L.WLf, WLf.data(), sizeof(float) * WLf.size()), "copy WLf");
+        CK(h2d(L.WSf, WSf.data(), sizeof(float) * WSf.size()), "copy WSf");
+        CK(cudaStreamSynchronize(st), "load sync");
+    }
+    CK(cudaStreamSynchronize(st), "load sync");
+
+    DevSystem &S = ctx->sys;
+    S.n_centres = b->n_centres;
+    S.n_shells = b->n_shells;
+    S.n_l = nl;
+    S.n_occ = n_occ;
+    S.n_vir = n_vir;
+    S.n_orb = no;
+    S.m = d.m;
+    S.n_tau = d.n_tau;
+    S.centres = ctx->at<double>(L.centres);
+    S.wcoef = ctx->at<double>(L.wcoef);
+    S.shell_centre = ctx->at<int>(L.shell_centre);
+    S.shell_alpha = ctx->at<double>(L.shell_alpha);
+    S.shell_coef = ctx->at<double>(L.shell_coef);
+    S.fn_shell = ctx->at<int>(L.fn_shell);
+    S.fn_pow = ctx->at<int>(L.fn_pow);
+    S.eps = ctx->at<double>(L.eps);
+    S.eps_homo = homo;
+    S.eps_lumo = lumo;
+    S.lambda = 2.0 * (lumo - homo);
+    S.Ng = Ng;
+    S.WL = ctx->at<double>(L.WL);
+    S.WS = ctx->at<double>(L.WS);
+    S.WLf = ctx->precision == MCMP2_MIXED ? ctx->at<float>(L.WLf) : nullptr;
+    S.WSf = ctx->precision == MCMP2_MIXED ? ctx->at<float>(L.WSf) : nullptr;
+
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, b->centres, sizeof(double) * 3 * b->n_centres);
+    h = fnv1a(h, b->weight, sizeof(double) * 4 * b->n_centres);
+    h = fnv1a(h, b->shell_centre, sizeof(int) * b->n_shells);
+    h = fnv1a(h, b->shell_l, sizeof(int) * b->n_shells);
+    h = fnv1a(h, b->shell_alpha, sizeof(double) * b->n_shells);
+    h = fnv1a(h, b->shell_coef, sizeof(double) * b->n_shells);
+    h = fnv1a(h, C, sizeof(double) * 2 * 4 * (size_t)nl * no);
+    h = fnv1a(h, eps, sizeof(double) * no);
+    ctx->digest = h;
+    ctx->loaded = true;
+    ctx->walkers = false;
+    if (ctx->precision == MCMP2_MIXED) {
+        const int rc = mixed_prepare(ctx->mixed, S, L.mixed, ctx->ws, ctx->err);
+        if (rc != MCMP2_OK) {
+            ctx->loaded = false;
+            return rc;
+        }
+    }
+    return MCMP2_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int reset_stats(mcmp2_ctx *ctx)
+{
+    CK(cudaMemsetAsync(ctx->ws + ctx->L.stats, 0, sizeof(Stats), ctx->stream), "reset stats");
+    return MCMP2_OK;
+}
+
+// The integrand engine for one step: from positions r and times (drawn or
+// given) to I'_n in out_slot.  Optionally updates statistics and advances the step.
+int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uint64_t seed, double *out_slot,
+                   int update, bool advance)
+{
+    const Layout &L = ctx->L;
+    const DevSystem &S = ctx->sys;
+    cudaStream_t st = ctx->stream;
+    unsigned long long *step = ctx->at<unsigned long long>(L.step);
+    double *a = ctx->at<double>(L.a);
+    double *tau = ctx->at<double>(L.tau);
+    double *scale = ctx->at<double>(L.scale);
+    double *partials = ctx->at<double>(L.partials);
+    CK(launch_pair_weights(S, r, a, st), "pair weights");
+    CK(launch_times(S, step, seed, tau_given, tau, scale, st), "imaginary times");
+    ctx->launches += 2;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->timing) {
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        ctx->pair_events.emplace_back(e0, e1);
+    }
+    if (ctx->precision == MCMP2_FP64) {
+        double *B = ctx->at<double>(L.B);
+        double *phi = ctx->at<double>(L.phi);
+        CK(launch_basis<double>(S, r, B, st), "basis values");
+        CK(launch_spinors_f64(S, B, phi, st), "spinor formation");
+        if (e0) CK(cudaEventRecord(e0, st), "event");
+        CK(launch_pairs_f64(S, phi, scale, a, partials, st), "pair-of-pairs tiles");
+        if (e1) CK(cudaEventRecord(e1, st), "event");
+        ctx->launches += 4;
+        ctx->pair_launches += 1;
+    } else {
+        float *B = ctx->at<float>(L.B);
+        float *phi = ctx->at<float>(L.phi);
+        CK(launch_basis<float>(S, r, B, st), "basis values");
+        CK(launch_spinors_f32(S, B, phi, st), "spinor formation");
+        int n_launch = 0, n_pair = 0;
+        const int rc = mixed_pairs(ctx->mixed, S, L.mixed, ctx->ws, phi, scale, a, partials, st, ctx->err, e0, e1,
+                                   &n_launch, &n_pair);
+        if (rc != MCMP2_OK) return rc;
+        ctx->launches += 3 + n_launch;
+        ctx->pair_launches += n_pair;
+    }
+    CK(launch_reduce(S, partials, L.n_tiles, out_slot, ctx->at<Stats>(L.stats), update, advance ? step : nullptr,
+                     st),
+       "step reduction");
+    ctx->launches += 1;
+    return MCMP2_OK;
+}
+
+bool all_finite(const double *x, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mcmp2_set_walkers(mcmp2_ctx *ctx, const double *r_host, uint64_t seed, int64_t burn_in)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
+    if (!r_host || burn_in < 0) return ctx->fail(MCMP2_EINVAL, "need initial positions and burn_in >= 0");
+    const size_t n = (size_t)ctx->dims.m * 6;
+    if (!all_finite(r_host, n)) return ctx->fail(MCMP2_ENONFINITE, "non-finite walker position");
+    const Layout &L = ctx->L;
+    cudaStream_t st = ctx->stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(ctx->ws + L.r, r_host, n * sizeof(double), cudaMemcpyHostToDevice, st), "copy walkers");
+    CK(cudaMemsetAsync(ctx->ws + L.step, 0, 8, st), "reset step");
+    int rc = reset_stats(ctx);
+    if (rc) return rc;
+    ctx->delta = MCMP2_DELTA0;
+    unsigned long long *step = ctx->at<unsigned long long>(L.step);
+    unsigned long long *acc = ctx->at<unsigned long long>(L.burn_acc);
+    int64_t done = 0;
+    while (done < burn_in) {
+        const int64_t len = std::min<int64_t>(MCMP2_ADAPT_WINDOW, burn_in - done);
+        CK(cudaMemsetAsync(acc, 0, 8, st), "reset acceptance");
+        for (int64_t i = 0; i < len; ++i) {
+            CK(launch_metropolis(ctx->sys, ctx->at<double>(L.r), step, seed, ctx->delta, acc, st), "metropolis");
+            CK(launch_advance_step(step, st), "advance step");
+        }
+        if (len == MCMP2_ADAPT_WINDOW) {
+            unsigned long long hacc = 0;
+            CK(cudaMemcpyAsync(&hacc, acc, 8, cudaMemcpyDeviceToHost, st), "read acceptance");
+            CK(cudaStreamSynchronize(st), "burn-in sync");
+            const double a = (double)hacc / (double)((long)ctx->dims.m * MCMP2_ADAPT_WINDOW);
+            double f = a / 0.5;
+            if (f > 2.0) f = 2.0;
+            if (f < 0.5) f = 0.5;
+            ctx->delta = ctx->delta * f;
+        }
+        done += len;
+    }
+    CK(cudaStreamSynchronize(st), "set_walkers sync");
+    ctx->walkers = true;
+    return MCMP2_OK;
+}
+
+int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->walkers) return ctx->fail(MCMP2_ENOTLOADED, "walkers not set");
+    if (n < 0) return ctx->fail(MCMP2_EINVAL, "n < 0");
+    const Layout &L = ctx->L;
+    cudaStream_t st = ctx->stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    Stats *stats = ctx->at<Stats>(L.stats);
+    double *r = ctx->at<double>(L.r);
+    for (int64_t i = 0; i < n; ++i) {
+        CK(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta, &stats->accepted, st),
+           "metropolis");
+        ctx->launches += 1;
+        const int rc = step_integrand(ctx, r, nullptr, seed, ctx->at<double>(L.per_step), 1, true);
+        if (rc) return rc;
+    }
+    if (out) {
+        Stats h;
+        CK(cudaMemcpyAsync(&h, stats, sizeof(Stats), cudaMemcpyDeviceToHost, st), "read statistics");
+        CK(cudaStreamSynchronize(st), "run_steps sync");
+        out->steps = h.steps;
+        out->n_blocks = h.n_blocks;
+        out->energy = h.n_blocks ? h.mean : 0.0;
+        out->variance = h.n_blocks ? h.m2 / (double)h.n_blocks : 0.0;
+        out->error = h.n_blocks ? std::sqrt(out->variance) / std::sqrt((double)h.n_blocks) : 0.0;
+        out->mean_all = h.steps ? h.all_sum / (double)h.steps : 0.0;
+        out->last_step = h.last;
+        out->accept_rate = h.steps ? (double)h.accepted / ((double)h.steps * ctx->dims.m) : 0.0;
+        if (!std::isfinite(h.all_sum) || !std::isfinite(h.mean) || !std::isfinite(h.m2))
+            return ctx->fail(MCMP2_ENONFINITE, "a step estimate is not finite");
+    }
+    return MCMP2_OK;
+}
+
+int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double *tau_host, double *out)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
+    if (n < 0 || (n > 0 && (!r_host || !tau_host || !out))) return ctx->fail(MCMP2_EINVAL, "bad replay arguments");
+    const int m = ctx->dims.m, nt = ctx->dims.n_tau;
+    if (!all_finite(r_host, (size_t)n * m * 6)) return ctx->fail(MCMP2_ENONFINITE, "non-finite position");
+    for (int64_t i = 0; i < n * nt; ++i)
+        if (!(tau_host[i] >= 0.0) || !std::isfinite(tau_host[i]))
+            return ctx->fail(MCMP2_EINVAL, "imaginary times must be finite and >= 0");
+    const Layout &L = ctx->L;
+    cudaStream_t st = ctx->stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    double *sr = ctx->at<double>(L.stage_r), *stau = ctx->at<double>(L.stage_tau);
+    double *slots = ctx->at<double>(L.per_step);
+    for (int64_t s0 = 0; s0 < n; s0 += REPLAY_CHUNK) {
+        const int len = (int)std::min<int64_t>(REPLAY_CHUNK, n - s0);
+        CK(cudaMemcpyAsync(sr, r_host + (size_t)s0 * m * 6, sizeof(double) * len * m * 6, cudaMemcpyHostToDevice, st),
+           "copy positions");
+        CK(cudaMemcpyAsync(stau, tau_host + (size_t)s0 * nt, sizeof(double) * len * nt, cudaMemcpyHostToDevice, st),
+           "copy times");
+        for (int j = 0; j < len; ++j) {
+            const int rc = step_integrand(ctx, sr + (size_t)j * m * 6, stau + (size_t)j * nt, 0, slots + j, 0, false);
+            if (rc) return rc;
+        }
+        CK(cudaMemcpyAsync(out + s0, slots, sizeof(double) * len, cudaMemcpyDeviceToHost, st), "copy results");
+        CK(cudaStreamSynchronize(st), "replay sync");
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(out[i])) return ctx->fail(MCMP2_ENONFINITE, "step %lld is not finite", (long long)i);
+    return MCMP2_OK;
+}
+
+int mcmp2_get_walkers(mcmp2_ctx *ctx, double *r_host, double *delta_host)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->walkers) return ctx->fail(MCMP2_ENOTLOADED, "walkers not set");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (r_host) {
+        CK(cudaMemcpyAsync(r_host, ctx->ws + ctx->L.r, sizeof(double) * 6 * ctx->dims.m, cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "copy walkers");
+        CK(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+    if (delta_host) *delta_host = ctx->delta;
+    return MCMP2_OK;
+}
+
+int mcmp2_debug_partials(mcmp2_ctx *ctx, double *out, size_t capacity, int *n_tiles, int *tile_pairs)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
+    if (n_tiles) *n_tiles = ctx->L.n_tiles;
+    if (tile_pairs) *tile_pairs = ctx->L.tile_pairs;
+    const size_t need = (size_t)ctx->L.n_tiles * ctx->dims.n_tau;
+    if (!out) return MCMP2_OK;
+    if (capacity < need) return ctx->fail(MCMP2_ENOSPACE, "need %zu doubles", need);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(out, ctx->ws + ctx->L.partials, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+       "copy partials");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return MCMP2_OK;
+}
+
+int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (mode == 1 || mode == 2) {
+        drop_events(ctx);
+        ctx->launches = ctx->pair_launches = 0;
+        ctx->timing = (mode == 1);
+        return MCMP2_OK;
+    }
+    if (mode != 0 || !out) return ctx->fail(MCMP2_EINVAL, "bad profile mode");
+    out->launches = ctx->launches;
+    out->pair_launches = ctx->pair_launches;
+    double ms = 0.0;
+    if (!ctx->pair_events.empty()) {
+        CK(cudaStreamSynchronize(ctx->stream), "sync");
+        for (auto &ev : ctx->pair_events) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ev.first, ev.second), "event time");
+            ms += t;
+        }
+    }
+    out->pair_ms = ms;
+    return MCMP2_OK;
+}
+
+int mcmp2_checkpoint_bytes(const mcmp2_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return MCMP2_EINVAL;
+    *bytes = sizeof(Checkpoint) + sizeof(double) * 6 * (size_t)ctx->dims.m;
+    return MCMP2_OK;
+}
+
+int mcmp2_checkpoint(mcmp2_ctx *ctx, void *buf, size_t capacity)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->walkers) return ctx->fail(MCMP2_ENOTLOADED, "walkers not set");
+    size_t need = 0;
+    mcmp2_checkpoint_bytes(ctx, &need);
+    if (!buf || capacity < need) return ctx->fail(MCMP2_ENOSPACE, "checkpoint needs %zu bytes", need);
+    Checkpoint ck{};
+    ck.magic = CK_MAGIC;
+    ck.version = 1;
+    ck.dims = ctx->dims;
+    ck.digest = ctx->digest;
+    ck.delta = ctx->delta;
+    cudaStream_t st = ctx->stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(&ck.step, ctx->ws + ctx->L.step, 8, cudaMemcpyDeviceToHost, st), "copy step");
+    CK(cudaMemcpyAsync(&ck.stats, ctx->ws + ctx->L.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st), "copy stats");
+    CK(cudaMemcpyAsync(static_cast<char *>(buf) + sizeof(Checkpoint), ctx->ws + ctx->L.r,
+                       sizeof(double) * 6 * ctx->dims.m, cudaMemcpyDeviceToHost, st),
+       "copy walkers");
+    CK(cudaStreamSynchronize(st), "sync");
+    std::memcpy(buf, &ck, sizeof(ck));
+    return MCMP2_OK;
+}
+
+int mcmp2_restore(mcmp2_ctx *ctx, const void *buf, size_t bytes)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
+    if (!buf || bytes < sizeof(Checkpoint)) return ctx->fail(MCMP2_EINVAL, "checkpoint truncated");
+    Checkpoint ck;
+    std::memcpy(&ck, buf, sizeof(ck));
+    if (ck.magic != CK_MAGIC || ck.version != 1) return ctx->fail(MCMP2_EINVAL, "not a checkpoint");
+    if (std::memcmp(&ck.dims, &ctx->dims, sizeof(mcmp2_dims)) != 0) return ctx->fail(MCMP2_EINVAL, "dims differ");
+    if (ck.digest != ctx->digest) return ctx->fail(MCMP2_EINVAL, "checkpoint belongs to another system");
+    const size_t need = sizeof(Checkpoint) + sizeof(double) * 6 * (size_t)ctx->dims.m;
+    if (bytes < need) return ctx->fail(MCMP2_EINVAL, "checkpoint truncated");
+    const double *r = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof(Checkpoint));
+    if (!all_finite(r, 6 * (size_t)ctx->dims.m) || !std::isfinite(ck.delta))
+        return ctx->fail(MCMP2_ENONFINITE, "checkpoint holds non-finite values");
+    cudaStream_t st = ctx->stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.step, &ck.step, 8, cudaMemcpyHostToDevice, st), "copy step");
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.stats, &ck.stats, sizeof(Stats), cudaMemcpyHostToDevice, st), "copy stats");
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.r, r, sizeof(double) * 6 * ctx->dims.m, cudaMemcpyHostToDevice, st),
+       "copy walkers");
+    CK(cudaStreamSynchronize(st), "sync");
+    ctx->delta = ck.delta;
+    ctx->walkers = true;
+    return MCMP2_OK;
+}
+
+}  // extern "C"
