@@ -424,12 +424,19 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
     CK(launch_pair_weights(S, r, a, st), "pair weights");
     CK(launch_times(S, step, seed, tau_given, tau, scale, st), "imaginary times");
     ctx->launches += 2;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int n_ev = ctx->precision == MCMP2_FP64 ? 1 : S.n_tau;
+    std::vector<cudaEvent_t> ev;
     if (ctx->timing) {
-        CK(cudaEventCreate(&e0), "event");
-        CK(cudaEventCreate(&e1), "event");
-        ctx->pair_events.emplace_back(e0, e1);
+        for (int i = 0; i < n_ev; ++i) {
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0), "event");
+            CK(cudaEventCreate(&e1), "event");
+            ctx->pair_events.emplace_back(e0, e1);
+            ev.push_back(e0);
+            ev.push_back(e1);
+        }
     }
+    cudaEvent_t e0 = ev.empty() ? nullptr : ev[0], e1 = ev.empty() ? nullptr : ev[1];
     if (ctx->precision == MCMP2_FP64) {
         double *B = ctx->at<double>(L.B);
         double *phi = ctx->at<double>(L.phi);
@@ -446,8 +453,8 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         CK(launch_basis<float>(S, r, B, st), "basis values");
         CK(launch_spinors_f32(S, B, phi, st), "spinor formation");
         int n_launch = 0, n_pair = 0;
-        const int rc = mixed_pairs(ctx->mixed, S, L.mixed, ctx->ws, phi, scale, a, partials, st, ctx->err, e0, e1,
-                                   &n_launch, &n_pair);
+        const int rc = mixed_pairs(ctx->mixed, S, L.mixed, ctx->ws, phi, scale, a, partials, st, ctx->err,
+                                   ev.empty() ? nullptr : ev.data(), &n_launch, &n_pair);
         if (rc != MCMP2_OK) return rc;
         ctx->launches += 3 + n_launch;
         ctx->pair_launches += n_pair;
@@ -544,6 +551,10 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
         if (!std::isfinite(h.all_sum) || !std::isfinite(h.mean) || !std::isfinite(h.m2))
             return ctx->fail(MCMP2_ENONFINITE, "a step estimate is not finite");
     }
+    if (ctx->precision == MCMP2_MIXED && out) {
+        const int rc = mixed_check_flag(ctx->mixed, ctx->ws, st, ctx->err);
+        if (rc) return rc;
+    }
     return MCMP2_OK;
 }
 
@@ -574,6 +585,10 @@ int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const doub
         }
         CK(cudaMemcpyAsync(out + s0, slots, sizeof(double) * len, cudaMemcpyDeviceToHost, st), "copy results");
         CK(cudaStreamSynchronize(st), "replay sync");
+    }
+    if (ctx->precision == MCMP2_MIXED) {
+        const int rc = mixed_check_flag(ctx->mixed, ctx->ws, st, ctx->err);
+        if (rc) return rc;
     }
     for (int64_t i = 0; i < n; ++i)
         if (!std::isfinite(out[i])) return ctx->fail(MCMP2_ENONFINITE, "step %lld is not finite", (long long)i);

@@ -25,11 +25,14 @@ struct MixedPlan {
 
 MixedLayout mixed_layout(int m, int n_occ, int n_vir, size_t offset);
 int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, std::string &err);
-// Issues the mixed-form contraction of one step (all n_tau times); records e0/e1
-// (if non-null) around the contraction kernels; reports the launches it made.
+// Issues the mixed-form contraction of one step (all n_tau times); if ev is
+// non-null, records ev[2t], ev[2t+1] around the contraction launch of time t;
+// reports the launches it made.
 int mixed_pairs(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const float *phi,
                 const double *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
-                cudaEvent_t e0, cudaEvent_t e1, int *n_launches, int *n_pair_launches);
+                cudaEvent_t *ev, int *n_launches, int *n_pair_launches);
+// Reads (synchronously) and clears the device flag a timed-out contraction sets.
+int mixed_check_flag(MixedPlan &plan, char *ws, cudaStream_t st, std::string &err);
 void mixed_release(MixedPlan &plan);
 
 cudaError_t launch_spinors_f32(const DevSystem &s, const float *B, float *phi, cudaStream_t st);

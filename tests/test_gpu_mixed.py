@@ -1,0 +1,120 @@
+"""The mixed-precision (split-BF16 x3 tensor-core) form against the oracle and the FP64 form."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_05632_gb300 as pkg
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+# Split BF16 x3 products carry ~2^-17 relative error per product and FP32
+# accumulation over <= 400 orbitals; the traced products of four propagator
+# blocks then agree with FP64 to ~1e-5 of their size.  Per-step estimates are
+# compared relative to max(|I'_n|, 1e-3 <|f|>) as in the FP64 tests.
+REL_MIXED = 2e-3
+
+
+def _rel(got, want, absmean):
+    scale = np.maximum(np.abs(want), 1e-3 * absmean)
+    return np.abs(got - want) / scale
+
+
+@pytest.fixture(scope="module")
+def medium():
+    return synthetic.make_system("medium")
+
+
+@pytest.fixture(scope="module")
+def medium_oracle(medium):
+    return oracle.Oracle(medium)
+
+
+@pytest.mark.parametrize("m,n_tau", [(16, 1), (13, 3), (2, 1), (33, 2)])
+def test_mixed_replay_matches_oracle_tiny(tiny, tiny_oracle, m, n_tau):
+    n = 3
+    r = synthetic.walker_positions(tiny.centres, n, m, seed=400 + m)
+    tau = synthetic.imaginary_times(tiny_oracle.lam(), n, n_tau, seed=9 + m)
+    ctx = pkg.Context(tiny, m, n_tau, pkg.MCMP2_MIXED)
+    got = ctx.eval_fixed(r, tau)
+    want, absmean = tiny_oracle.eval_steps(r, tau, with_abs=True)
+    assert np.all(_rel(got, want, absmean) <= REL_MIXED), (got, want)
+
+
+def test_mixed_replay_matches_oracle_medium_system(medium, medium_oracle):
+    m, n_tau = 40, 2
+    r = synthetic.walker_positions(medium.centres, 1, m, seed=41)
+    tau = synthetic.imaginary_times(medium_oracle.lam(), 1, n_tau, seed=42)
+    ctx = pkg.Context(medium, m, n_tau, pkg.MCMP2_MIXED)
+    got = ctx.eval_fixed(r, tau)
+    want, absmean = medium_oracle.eval_steps(r, tau, with_abs=True)
+    assert np.all(_rel(got, want, absmean) <= REL_MIXED), (got, want)
+
+
+def _tile_pairs(bp, bq, tp, m):
+    ps, qs = [], []
+    for i in range(tp):
+        for j in range(tp):
+            p, q = bp * tp + i, bq * tp + j
+            if p < m and q < m and (bp < bq or i < j):
+                ps.append(p)
+                qs.append(q)
+    return np.array(ps), np.array(qs)
+
+
+def test_mixed_full_size_sampled_tiles_match_oracle(medium, medium_oracle):
+    """The bench configuration: m = 1024, 4 times; sampled 16 x 16 tiles vs the oracle."""
+    m, n_tau = 1024, 4
+    r = synthetic.walker_positions(medium.centres, 1, m, seed=51)
+    tau = synthetic.imaginary_times(medium_oracle.lam(), 1, n_tau, seed=52)
+    ctx = pkg.Context(medium, m, n_tau, pkg.MCMP2_MIXED)
+    step = ctx.eval_fixed(r, tau)[0]
+    partials, tp = ctx.debug_partials()
+    assert tp == 16
+    nb = (m + tp - 1) // tp
+    assert step == pytest.approx(partials.sum() / (m * (m - 1) / 2) / n_tau, rel=1e-12)
+    for bp, bq in [(0, 0), (0, 1), (7, 40), (nb - 1, nb - 1), (31, nb - 1)]:
+        ps, qs = _tile_pairs(bp, bq, tp, m)
+        vals = medium_oracle.eval_pairs(r[0], tau[0], ps, qs)
+        want = vals.sum(axis=0)
+        k = sum(nb - b for b in range(bp)) + (bq - bp)
+        got = partials[:, k]
+        scale = np.maximum(np.abs(want), 1e-3 * np.abs(vals).sum(axis=0))
+        assert np.all(np.abs(got - want) <= REL_MIXED * scale), (bp, bq, got, want)
+
+
+def test_mixed_agrees_with_fp64_form_within_a_fifth_of_sigma(medium):
+    """Same walk (FP64 sampling in both forms), mixed vs FP64 estimates:
+    the mean difference is far below 0.2 sigma-bar of the FP64 run."""
+    m, n_tau, seed, n = 96, 2, 808, 400
+    r0 = synthetic.walker_positions(medium.centres, 1, m, seed=3)[0]
+    per = {}
+    for prec in (pkg.MCMP2_FP64, pkg.MCMP2_MIXED):
+        ctx = pkg.Context(medium, m, n_tau, prec)
+        ctx.set_walkers(r0, seed, 100)
+        vals = []
+        for _ in range(n):
+            vals.append(ctx.run_steps(1, seed)["last_step"])
+        per[prec] = np.array(vals)
+        ctx.close()
+    d = per[pkg.MCMP2_MIXED] - per[pkg.MCMP2_FP64]
+    I, s2, sb, nb = oracle.blocking(per[pkg.MCMP2_FP64])
+    assert nb == 4
+    assert abs(d.mean()) < 0.2 * sb, (d.mean(), sb)
+    absmean = np.abs(per[pkg.MCMP2_FP64]).mean()
+    assert np.max(np.abs(d)) < REL_MIXED * absmean
+
+
+def test_mixed_walk_statistics_and_checkpoint(tiny_soft):
+    m, seed = 16, 21
+    r0 = synthetic.walker_positions(tiny_soft.centres, 1, m, seed=2)[0]
+    ctx = pkg.Context(tiny_soft, m, 1, pkg.MCMP2_MIXED)
+    ctx.set_walkers(r0, seed, 50)
+    ctx.run_steps(120, seed)
+    blob = ctx.checkpoint()
+    a = ctx.run_steps(90, seed)
+    other = pkg.Context(tiny_soft, m, 1, pkg.MCMP2_MIXED)
+    other.restore(blob)
+    b = other.run_steps(90, seed)
+    assert a == b
+    assert a["steps"] == 210 and a["n_blocks"] == 2 and np.isfinite(a["energy"])
