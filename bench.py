@@ -174,6 +174,8 @@ def main():
     ap.add_argument("--stat-steps", type=int, default=10000, help="steps of the run that estimates sigma for time-to-0.1%%")
     ap.add_argument("--cpu-sample-m", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--m", type=int, default=M, help="walker pairs (the workload is m=1024; smaller m only "
+                                                     "for sized profiler captures)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -199,13 +201,14 @@ def main():
     peaks, peak_kind = load_peaks()
     prec = pkg.MCMP2_MIXED if args.precision == "mixed" else pkg.MCMP2_FP64
     seed = 5632 + rank
-    samples_per_step = M * (M - 1) // 2 * N_TAU
+    m_run = args.m
+    samples_per_step = m_run * (m_run - 1) // 2 * N_TAU
     flop_unit = flops_per_sample(system.n_occ, system.n_vir)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     def make_ctx(p):
-        ctx = pkg.Context(system, M, N_TAU, p, device=local)
-        r0 = synthetic.walker_positions(system.centres, 1, M, seed=seed)[0]
+        ctx = pkg.Context(system, m_run, N_TAU, p, device=local)
+        r0 = synthetic.walker_positions(system.centres, 1, m_run, seed=seed)[0]
         ctx.set_walkers(r0, seed, 200)
         return ctx
 
@@ -241,7 +244,7 @@ def main():
     # End to end through the public replay call: host positions and times from
     # pinned memory copied in, the step estimate copied out, every step.
     e2e_steps = max(3, min(args.steps, 50))
-    r_host = torch.from_numpy(synthetic.walker_positions(system.centres, e2e_steps, M, seed=seed + 7)).pin_memory()
+    r_host = torch.from_numpy(synthetic.walker_positions(system.centres, e2e_steps, m_run, seed=seed + 7)).pin_memory()
     lam = 2.0 * (system.eps[system.n_occ:].min() - system.eps[:system.n_occ].max())
     t_host = torch.from_numpy(synthetic.imaginary_times(lam, e2e_steps, N_TAU, seed=seed + 8)).pin_memory()
     o_host = torch.zeros(e2e_steps, dtype=torch.float64).pin_memory()
@@ -302,10 +305,11 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16x3" if prec == pkg.MCMP2_MIXED else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between timed steps",
+            "config": {"workload": WORKLOAD if m_run == M else WORKLOAD.replace("m=1024", f"m={m_run}"),
+                       "precision": args.precision, "l2": "flushed between timed steps",
                        "parallelism": f"{world} independent replicas"},
             "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": M * 6 * 8 + N_TAU * 8,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": m_run * 6 * 8 + N_TAU * 8,
                     "d2h_bytes_per_step": 8, "call": "mcmp2_eval_fixed, pinned host buffers"},
             "gpu_launches": prof["launches"],
             "roofline": roof,
