@@ -184,6 +184,48 @@ int mcmp2_checkpoint_bytes(const mcmp2_ctx *ctx, size_t *bytes);
 int mcmp2_checkpoint(mcmp2_ctx *ctx, void *buf_host, size_t capacity);
 int mcmp2_restore(mcmp2_ctx *ctx, const void *buf_host, size_t bytes);
 
+/* Allocation-free evaluation of one step estimate from given spinor values.
+ *
+ * The paper has no counterpart: this call exists for callers that cannot
+ * allocate device memory.  Some programs reserve their whole device-memory
+ * budget up front and hand it to their own pool, so a later cudaMalloc (or a
+ * framework allocator) would fail or is forbidden; others run this work in a
+ * section of their program that must never call into an allocator.  Such a
+ * caller cannot create the workspace the other entry points need.
+ *
+ * It computes the same quantity as the contraction and reduction of the FP64
+ * form: I'_n = (1/n_tau) sum_t (1/mC2) sum_{p<q} Re f/(w w w), and writes it
+ * to out.  Inputs, all device pointers on the current device:
+ *   phi   [8m][n_occ + n_vir] complex (re, im doubles): spinor value phi_k^c at
+ *         row 4 x + c, position x = 2p + e (electron e of walker pair p),
+ *         c = L-alpha, L-beta, S-alpha, S-beta; occupied columns first;
+ *   scale [n_tau][n_occ + n_vir]: exp((eps_i - eps_HOMO) tau_t / 2) for
+ *         occupied and exp(-(eps_a - eps_LUMO) tau_t / 2) for virtual spinors;
+ *   a     [m]: N_g / (g(r1p) g(r2p));
+ *   lambda = 2 (eps_LUMO - eps_HOMO) > 0;
+ *   out   one double (device), written on cuda_stream.
+ * Work is issued on cuda_stream (a cudaStream_t, NULL for the legacy default
+ * stream); the call does not wait for it.
+ *
+ * Scratch: the per-tile partial sums live in a fixed array of
+ * MCMP2_NOALLOC_MAX_PARTIALS doubles (512 KiB) inside the library, held on
+ * every GPU that loads the library until the process exits.  It needs
+ * n_tau * ceil(m/8) (ceil(m/8) + 1) / 2 <= MCMP2_NOALLOC_MAX_PARTIALS (for
+ * example m = 1024 with n_tau <= 7); larger sizes return MCMP2_ENOSPACE
+ * before any work is issued.  The array is shared by all calls and keeps the
+ * last call's contents; every entry a call reads is first written by that
+ * call, so nothing needs clearing.  Calls that overlap on the GPU (on
+ * different streams, or from different threads) race on the array and give
+ * wrong results: serialise them.  The first call on each device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture.  No cudaMalloc, cudaFree or other allocating
+ * routine is called.
+ * Returns MCMP2_OK, MCMP2_EINVAL (bad sizes, null pointers, lambda), MCMP2_ENOSPACE
+ * (sizes beyond the scratch array) or MCMP2_ECUDA (a launch failed). */
+#define MCMP2_NOALLOC_MAX_PARTIALS 65536
+int mcmp2_pair_sum_f64_noalloc(int m, int n_occ, int n_vir, int n_tau, const double *phi, const double *scale,
+                               const double *a, double lambda, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

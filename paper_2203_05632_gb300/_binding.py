@@ -74,6 +74,7 @@ SIGNATURES = {
     "mcmp2_debug_partials": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mcmp2_profile": (_I, [_P, _I, ctypes.POINTER(ProfileCounters)]),
     "mcmp2_checkpoint_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
+    "mcmp2_pair_sum_f64_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, ctypes.c_double, _P, _P]),
     "mcmp2_checkpoint": (_I, [_P, _P, _SZ]),
     "mcmp2_restore": (_I, [_P, _P, _SZ]),
 }
@@ -240,3 +241,18 @@ class Context:
 
 def tile_pairs_of(precision: int) -> int:
     return 8 if precision == MCMP2_FP64 else 16
+
+
+def pair_sum_f64_noalloc(m, n_occ, n_vir, n_tau, phi, scale, a, lam, out, stream=None):
+    """Allocation-free step estimate (mcmp2_pair_sum_f64_noalloc) on device tensors.
+
+    For callers that cannot allocate device memory: the library's own fixed
+    scratch array holds the intermediate sums.  phi, scale, a and out are
+    CUDA tensors the caller already owns (layouts as in include/mcmp2.h)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = load_library().mcmp2_pair_sum_f64_noalloc(int(m), int(n_occ), int(n_vir), int(n_tau),
+                                                   _P(phi.data_ptr()), _P(scale.data_ptr()), _P(a.data_ptr()),
+                                                   float(lam), _P(out.data_ptr()), _P(st.cuda_stream))
+    if rc != MCMP2_OK:
+        raise McMp2Error(rc, "mcmp2_pair_sum_f64_noalloc failed")
