@@ -36,7 +36,6 @@ struct DevSystem {
     double eps_homo, eps_lumo, lambda, Ng;
     const double *WL;          // FP64 large operand [n_l][2][n_orb][2] (L-alpha, L-beta; re, im)
     const double *WS;          // FP64 small operand [3 n_l][2][n_orb][2] (S-alpha, S-beta)
-    const float *WLf, *WSf;    // FP32 copies for the mixed form
 };
 
 // ---------------------------------------------------------------------------

@@ -52,7 +52,6 @@ cudaError_t launch_basis(const DevSystem &s, const double *r, T *B, cudaStream_t
     return cudaGetLastError();
 }
 template cudaError_t launch_basis<double>(const DevSystem &, const double *, double *, cudaStream_t);
-template cudaError_t launch_basis<float>(const DevSystem &, const double *, float *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Row-major C[M x N] = A[M x K] B[K x N]: 64 x 64 tiles, 4 x 4 per thread.
@@ -118,14 +117,6 @@ cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi,
     cudaError_t e = gemm_rm<double>(P, n4, s.n_l, B, 4 * s.n_l, s.WL, n4, phi, ld, st);
     if (e != cudaSuccess) return e;
     return gemm_rm<double>(P, n4, 3 * s.n_l, B + s.n_l, 4 * s.n_l, s.WS, n4, phi + n4, ld, st);
-}
-
-cudaError_t launch_spinors_f32(const DevSystem &s, const float *B, float *phi, cudaStream_t st)
-{
-    const int P = 2 * s.m, n4 = 4 * s.n_orb, ld = 8 * s.n_orb;
-    cudaError_t e = gemm_rm<float>(P, n4, s.n_l, B, 4 * s.n_l, s.WLf, n4, phi, ld, st);
-    if (e != cudaSuccess) return e;
-    return gemm_rm<float>(P, n4, 3 * s.n_l, B + s.n_l, 4 * s.n_l, s.WSf, n4, phi + n4, ld, st);
 }
 
 // ---------------------------------------------------------------------------

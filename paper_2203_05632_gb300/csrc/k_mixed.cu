@@ -1,180 +1,346 @@
-// Mixed-precision propagator contraction on the tcgen05 tensor cores (sm_103a).
+// Mixed-precision integrand engine on the tcgen05 tensor cores (sm_103a).
 //
-// For each imaginary time the scaled spinor values X(x)_ck = phi_k^c(x) s_k(tau)
-// (rows x,c = 8p + 4e + c for electron e of walker pair p) are split into
-// BF16 hi/lo planes of their real and imaginary parts.  A tile of 16 p-pairs
-// x 16 q-pairs computes, for all 128 x 128 (row, column) pairs,
-//   G(x, y)_cd = sum_k X(x)_ck conj(X(y)_dk)
-//   Re G = Xr Yr^T + Xi Yi^T,   Im G = Xi Yr^T - Xr Yi^T,
-// each real product as hi*hi + hi*lo + lo*hi (split BF16 x3, FP32 accumulate
-// in tensor memory), over the occupied spinors (G-) and the virtual ones (G+).
-// The epilogue forms the direct and exchange traces of the trace form of
-// Eq. MCMP2 for every pair of pairs of the tile and accumulates
-// Re f / (w w w) in FP64.
-//
-// Roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1 allocates tensor
-// memory and lane 0 issues the MMAs, warps 2..5 run the epilogue (one per
-// tensor-memory lane quarter).  Every wait is bounded in time; on a time-out
-// the kernel records it in a flag, stops, waits (bounded) for its own copies,
-// frees tensor memory and returns, and the host reports MCMP2_ETIMEOUT.
+// Per step:
+//  1. basis_split_kernel: basis values and gradients at the 2m positions (FP32)
+//     as BF16 hi/lo planes (value = hi + lo to ~2^-17).
+//  2. spinor_mixed_kernel: spinor formation (Eq. C with kinetic balance) as a
+//     real split-BF16 x3 GEMM, phi = [g | grad g] x W (W = C folded with the
+//     Pauli matrices), FP32 accumulate in tensor memory.  Its epilogue scales
+//     the spinor values by s_k(tau) for every imaginary time and writes the
+//     BF16 hi/lo planes of X(x)_ck = phi_k^c(x) s_k(tau): rows 4x + c,
+//     occupied and virtual orbitals in separate planes.
+//  3. pairs_mixed_kernel: for every (16 x 16 walker-pair tile, tau) the
+//     Hermitian products G(x, y)_cd = sum_k X(x)_ck conj(X(y)_dk) over the
+//     occupied (G-) and virtual (G+) orbitals,
+//       Re G = Xr Yr^T + Xi Yi^T,  Im G = Xi Yr^T - Xr Yi^T,
+//     each real product as hi*hi + hi*lo + lo*hi (12 MMAs per 16-deep K step),
+//     then the direct and exchange traces of the trace form of Eq. MCMP2 for
+//     every pair of pairs, accumulated in FP64 as Re f / (w w w).
+// Every wait is bounded in time; on a time-out a kernel records it in a flag,
+// stops, drains its own copies, frees tensor memory and returns, and the host
+// reports MCMP2_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cstring>
+#include <vector>
 
 #include "../../include/mcmp2.h"
 #include "mixed.cuh"
+#include "tc_common.cuh"
 
 namespace mcmp2 {
 
+using namespace tc;
+
 namespace {
 
-constexpr int BM = 128;                   // rows per tile side (16 walker pairs x 8)
-constexpr int BK = 32;                    // K elements per stage (64 bytes: one 64B swizzle row)
-constexpr int STAGES = 3;
-constexpr int PLANE_TILE = BM * BK * 2;   // 8 KB
-constexpr int STAGE_BYTES = 8 * PLANE_TILE;  // A and B, 4 planes each
-constexpr int TMEM_COLS = 512;            // G+ re | G+ im | G- re | G- im, 128 columns each
-constexpr int THREADS = 192;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
+constexpr int BK = 32;                                    // K elements per stage row (64 B, one swizzle row)
+constexpr int TILE_BYTES = 128 * BK * 2;                  // one 128 x 32 BF16 operand tile (8 KB)
 
-struct MixedMaps {
-    CUtensorMap m[8];  // [occ 0..3 | vir 4..7]: re_hi, re_lo, im_hi, im_lo
-};
+__device__ __forceinline__ int n_chunks(int k) { return (k + BK - 1) / BK; }
 
-struct MixedArgs {
-    const double *a;      // [m] pair weight factors N_g / (g1 g2)
-    double *partials;     // [n_tau][n_tiles]
-    int *abort_flag;      // set to a nonzero code on a time-out
-    int m, n_tiles, nb, t_index, n_occ, n_vir;
-    double inv_lambda;
-};
-
-struct SmemLayout {
-    static constexpr int stages_off = 0;
-    static constexpr int bars_off = STAGES * STAGE_BYTES;  // full[S], empty[S], tmem_full, tmem_empty
-    static constexpr int tmem_slot_off = bars_off + (2 * STAGES + 2) * 8;
-    static constexpr int red_off = tmem_slot_off + 16;     // 16 doubles: per-pair-group partial sums
-    static constexpr int total = red_off + 16 * 8;
-};
-constexpr int SMEM_BYTES = SmemLayout::total + 1024;  // slack for 1024-byte alignment
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long globaltimer()
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+// ===========================================================================
+// 1. Basis values as split BF16 planes
+// ===========================================================================
+__global__ void basis_split_kernel(DevSystem s, const double *__restrict__ r, __nv_bfloat16 *__restrict__ BLh,
+                                   __nv_bfloat16 *__restrict__ BLl, __nv_bfloat16 *__restrict__ BSh,
+                                   __nv_bfloat16 *__restrict__ BSl, int nl_pad, int nl3_pad)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on a barrier phase.  Returns false (after recording `code`) on a
-// time-out, or if another role has already aborted.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort_flag, int code)
-{
-    const unsigned long long t0 = globaltimer();
-    for (uint32_t i = 0;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 63) {
-            if (*(volatile int *)abort_flag) return false;
-            if (globaltimer() - t0 > TIMEOUT_NS) {
-                atomicCAS(abort_flag, 0, code);
-                return false;
-            }
+    const int x = blockIdx.y;
+    const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mu >= s.n_l) return;
+    const int sh = s.fn_shell[mu];
+    const double *A = s.centres + 3 * s.shell_centre[sh];
+    const float d[3] = {(float)(r[3 * x + 0] - A[0]), (float)(r[3 * x + 1] - A[1]), (float)(r[3 * x + 2] - A[2])};
+    const float al = (float)s.shell_alpha[sh];
+    const float e = (float)s.shell_coef[sh] * __expf(-al * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    const int pw[3] = {s.fn_pow[3 * mu], s.fn_pow[3 * mu + 1], s.fn_pow[3 * mu + 2]};
+    float pk[3], dk[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float v = 1.f, lower = 0.f;
+        for (int i = 0; i < pw[j]; ++i) v *= d[j];
+        if (pw[j] > 0) {
+            lower = 1.f;
+            for (int i = 0; i < pw[j] - 1; ++i) lower *= d[j];
+            lower *= (float)pw[j];
+        }
+        pk[j] = v;
+        dk[j] = lower - 2.f * al * v * d[j];
+    }
+    float vals[4] = {pk[0] * pk[1] * pk[2] * e, dk[0] * pk[1] * pk[2] * e, pk[0] * dk[1] * pk[2] * e,
+                     pk[0] * pk[1] * dk[2] * e};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(vals[j]);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(vals[j] - __bfloat162float(hi));
+        if (j == 0) {
+            BLh[(size_t)x * nl_pad + mu] = hi;
+            BLl[(size_t)x * nl_pad + mu] = lo;
+        } else {
+            const size_t o = (size_t)x * nl3_pad + (size_t)(j - 1) * s.n_l + mu;
+            BSh[o] = hi;
+            BSl[o] = lo;
         }
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+// ===========================================================================
+// 2. Spinor formation with fused scale-and-split epilogue
+// ===========================================================================
+constexpr int SP_STAGES = 4;
+constexpr int SP_STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo
+constexpr int SP_THREADS = 192;                 // TMA warp, MMA warp, 4 epilogue warps
+constexpr int SP_TMEM_COLS = 256;               // two 128-column accumulators
+constexpr int SP_BARS_OFF = SP_STAGES * SP_STAGE_BYTES;
+constexpr int SP_SMEM = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16 + 1024;
+
+struct SpinorMaps {
+    CUtensorMap m[8];  // 0..3: A_L hi, A_L lo, B_L hi, B_L lo; 4..7: the same for the gradient part
+};
+
+struct SpinorArgs {
+    const double *scale;  // [n_tau][n_orb]
+    __nv_bfloat16 *occ;   // [n_tau][4][rows][k_occ_pad]
+    __nv_bfloat16 *vir;   // [n_tau][4][rows][k_vir_pad]
+    int *abort_flag;
+    int P, nl, n_mt, n_kb, n_kb_occ, n_occ, n_vir, n_orb, n_tau, rows, k_occ_pad, k_vir_pad;
+};
+
+__device__ __forceinline__ void sp_tile(int tile, int n_kb, int &mt, int &c4, int &kb)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
+    const int per = 4 * n_kb;
+    mt = tile / per;
+    const int nt = tile - mt * per;
+    c4 = nt / n_kb;
+    kb = nt - c4 * n_kb;
 }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle (8 rows x 64 B atoms,
-// stride 512 B between 8-row groups), SM100 descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+__global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __grid_constant__ SpinorMaps maps,
+                                                                     const SpinorArgs args)
 {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(16u >> 4) << 16;   // leading-dimension offset (unused for swizzled K-major)
-    d |= (uint64_t)(512u >> 4) << 32;  // stride-dimension offset
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)4 << 61;            // SWIZZLE_64B
-    return d;
-}
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + SP_BARS_OFF);
+    uint64_t *empty = full + SP_STAGES;
+    uint64_t *tfull = empty + SP_STAGES;  // [2]
+    uint64_t *tempty = tfull + 2;         // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = args.n_mt * 4 * args.n_kb;
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = N = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(bool negate_a)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((negate_a ? 1u : 0u) << 13) | ((uint32_t)(128 >> 3) << 17) |
-           ((uint32_t)(128 >> 4) << 24);
-}
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SP_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init_fence();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, SP_TMEM_COLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int i = 0; i < 8; ++i) tma_prefetch(&maps.m[i]);
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[SP_STAGES] = {};
+            uint32_t issued_phase[SP_STAGES] = {};
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                int mt, c4, kb;
+                sp_tile(tile, args.n_kb, mt, c4, kb);
+                const bool grad = c4 >= 2;
+                const CUtensorMap *mp = &maps.m[grad ? 4 : 0];
+                const int K = grad ? 3 * args.nl : args.nl;
+                const int wt_row = ((c4 & 1) * args.n_kb + kb) * 128;
+                for (int c = 0; c < n_chunks(K); ++c) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, args.abort_flag, 11, TIMEOUT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *st = smem + stage * SP_STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[stage], SP_STAGE_BYTES);
+                    tma_load_2d(st + 0 * TILE_BYTES, mp + 0, &full[stage], c * BK, mt * 128);
+                    tma_load_2d(st + 1 * TILE_BYTES, mp + 1, &full[stage], c * BK, mt * 128);
+                    tma_load_2d(st + 2 * TILE_BYTES, mp + 2, &full[stage], c * BK, wt_row);
+                    tma_load_2d(st + 3 * TILE_BYTES, mp + 3, &full[stage], c * BK, wt_row);
+                    issued[stage] = 1;
+                    issued_phase[stage] = phase;
+                    if (++stage == SP_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok)
+                for (int s = 0; s < SP_STAGES; ++s)
+                    if (issued[s]) mbar_drain(&full[s], issued_phase[s], TIMEOUT_NS);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0, buf = 0;
+            uint32_t phase = 0, tphase[2] = {0, 0};
+            bool ok = true;
+            const uint32_t id = idesc_bf16(128, false);
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                int mt, c4, kb;
+                sp_tile(tile, args.n_kb, mt, c4, kb);
+                const int K = c4 >= 2 ? 3 * args.nl : args.nl;
+                if (!mbar_wait(&tempty[buf], tphase[buf] ^ 1u, args.abort_flag, 12, TIMEOUT_NS)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t d = tmem + 128u * buf;
+                for (int c = 0; c < n_chunks(K); ++c) {
+                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 13, TIMEOUT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const int kvalid = K - c * BK;
+                    const int ksteps = kvalid >= BK ? BK / 16 : (kvalid + 15) / 16;
+                    const uint32_t base = smem_u32(smem + stage * SP_STAGE_BYTES);
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint32_t off = ks * 32;
+                        const uint64_t ah = sdesc_sw64(base + 0 * TILE_BYTES + off);
+                        const uint64_t al = sdesc_sw64(base + 1 * TILE_BYTES + off);
+                        const uint64_t bh = sdesc_sw64(base + 2 * TILE_BYTES + off);
+                        const uint64_t bl = sdesc_sw64(base + 3 * TILE_BYTES + off);
+                        umma(d, ah, bh, id, (c == 0 && ks == 0) ? 0u : 1u);
+                        umma(d, ah, bl, id, 1u);
+                        umma(d, al, bh, id, 1u);
+                    }
+                    umma_commit(&empty[stage]);
+                    if (++stage == SP_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&tfull[buf]);
+                tphase[buf] ^= 1u;
+                buf ^= 1;
+            }
+            // Let every MMA this thread issued finish before tensor memory is freed.
+            umma_commit(&empty[stage]);
+            mbar_drain(&empty[stage], phase, TIMEOUT_NS);
+        }
+    } else {
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+        int buf = 0;
+        uint32_t ephase[2] = {0, 0};
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            int mt, c4, kb;
+            sp_tile(tile, args.n_kb, mt, c4, kb);
+            const bool got = mbar_wait(&tfull[buf], ephase[buf], args.abort_flag, 14, TIMEOUT_NS);
+            if (bar_any<1, 128>(!got)) break;
+            ephase[buf] ^= 1u;
+            fence_after();
+            const int x = mt * 128 + row;
+            const bool occ = kb < args.n_kb_occ;
+            const int kl = occ ? kb : kb - args.n_kb_occ;
+            const int kpad = occ ? args.k_occ_pad : args.k_vir_pad;
+            const int k_base = occ ? 0 : args.n_occ;              // absolute index of the region's first orbital
+            const int k_end = occ ? args.n_occ : args.n_orb;      // one past the region's last orbital
+            __nv_bfloat16 *planes = occ ? args.occ : args.vir;
+            const size_t plane_elems = (size_t)args.rows * kpad;
+            const size_t row_off = (size_t)(4 * x + c4) * kpad;
+            for (int j = 0; j < 4; ++j) {
+                float re[16], im[16];
+                tmem_ld<16>(lane_addr + 128u * buf + 16u * j, re);
+                tmem_ld<16>(lane_addr + 128u * buf + 64u + 16u * j, im);
+                tmem_wait_ld();
+                if (x < args.P) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+                    for (int g = 0; g < 2; ++g) {
+                        const int col = kl * 64 + 16 * j + 8 * g;
+                        if (col >= kpad) continue;
+                        for (int t = 0; t < args.n_tau; ++t) {
+                            uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                            for (int i = 0; i < 8; i += 2) {
+                                const int k0 = k_base + col + i;
+                                const float s0 = k0 < k_end ? (float)args.scale[(size_t)t * args.n_orb + k0] : 0.f;
+                                const float s1 =
+                                    k0 + 1 < k_end ? (float)args.scale[(size_t)t * args.n_orb + k0 + 1] : 0.f;
+                                const float xr0 = re[8 * g + i] * s0, xr1 = re[8 * g + i + 1] * s1;
+                                const float xi0 = im[8 * g + i] * s0, xi1 = im[8 * g + i + 1] * s1;
+                                const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
+                                const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
+                                rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
+                                ih[i / 2] = *reinterpret_cast<const uint32_t *>(&hi);
+                                rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
+                                il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
+                            }
+                            __nv_bfloat16 *dst = planes + (size_t)t * 4 * plane_elems + row_off + col;
+                            *reinterpret_cast<uint4 *>(dst) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                            *reinterpret_cast<uint4 *>(dst + plane_elems) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                            *reinterpret_cast<uint4 *>(dst + 2 * plane_elems) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                            *reinterpret_cast<uint4 *>(dst + 3 * plane_elems) = make_uint4(il[0], il[1], il[2], il[3]);
+                        }
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            buf ^= 1;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, SP_TMEM_COLS);
+    }
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// ===========================================================================
+// 3. Pair-of-pairs contraction with the trace epilogue
+// ===========================================================================
+constexpr int PR_STAGES = 3;
+constexpr int PR_STAGE_BYTES = 8 * TILE_BYTES;  // A: re_hi, re_lo, im_hi, im_lo; B: the same
+constexpr int PR_EPI_WARPS = 8;                 // two per tensor-memory lane quarter
+constexpr int PR_THREADS = 64 + 32 * PR_EPI_WARPS;
+constexpr int PR_TMEM_COLS = 512;               // G+ re | G+ im | G- re | G- im
+constexpr int PR_BARS_OFF = PR_STAGES * PR_STAGE_BYTES;
+constexpr int PR_RED_OFF = PR_BARS_OFF + (2 * PR_STAGES + 2) * 8 + 16;
+constexpr int PR_SMEM = PR_RED_OFF + 32 * 8 + 1024;
 
-__device__ __forceinline__ void tile_coords(int tile, int nb, int &bp, int &bq)
+struct PairMaps {
+    CUtensorMap occ, vir;  // 3-D: (orbital, row, 4 tau + plane)
+};
+
+struct PairArgs {
+    const double *a;   // [m] pair weight factors N_g / (g1 g2)
+    double *partials;  // [n_tau][n_tiles]
+    int *abort_flag;
+    int m, n_tiles, nb, n_tau, n_occ, n_vir;
+    double inv_lambda;
+};
+
+__device__ __forceinline__ void pair_tile(int tile, int nb, int &bp, int &bq)
 {
     int k = tile, b = 0;
     while (k >= nb - b) {
@@ -185,55 +351,34 @@ __device__ __forceinline__ void tile_coords(int tile, int nb, int &bp, int &bq)
     bq = b + k;
 }
 
-__device__ __forceinline__ int k_chunks(int n) { return (n + BK - 1) / BK; }
-
-// OR of a predicate over the 128 epilogue threads (named barrier 1).
-__device__ __forceinline__ bool epilogue_any(bool v)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, 128, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v)
-        : "memory");
-    return r != 0;
-}
-
-__global__ void __launch_bounds__(THREADS, 1) pairs_mixed_kernel(const __grid_constant__ MixedMaps maps,
-                                                                 const MixedArgs args)
+__global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid_constant__ PairMaps maps,
+                                                                    const PairArgs args)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + SmemLayout::bars_off);
-    uint64_t *empty = full + STAGES;
-    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + PR_BARS_OFF);
+    uint64_t *empty = full + PR_STAGES;
+    uint64_t *tmem_full = empty + PR_STAGES;
     uint64_t *tmem_empty = tmem_full + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SmemLayout::tmem_slot_off);
-    double *red = reinterpret_cast<double *>(smem + SmemLayout::red_off);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 1);
+    double *red = reinterpret_cast<double *>(smem + PR_RED_OFF);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_occ_chunks = k_chunks(args.n_occ), n_vir_chunks = k_chunks(args.n_vir);
+    const int n_occ_chunks = n_chunks(args.n_occ), n_vir_chunks = n_chunks(args.n_vir);
     const int chunks_per_tile = n_occ_chunks + n_vir_chunks;
+    const int n_items = args.n_tiles * args.n_tau;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < PR_STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(tmem_full, 1);
-        mbar_init(tmem_empty, 4);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init(tmem_empty, PR_EPI_WARPS);
+        mbar_init_fence();
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 1) tmem_alloc(tmem_slot, PR_TMEM_COLS);
     fence_before();
     __syncthreads();
     fence_after();
@@ -242,48 +387,43 @@ __global__ void __launch_bounds__(THREADS, 1) pairs_mixed_kernel(const __grid_co
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            for (int s = 0; s < 8; ++s)
-                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[s])) : "memory");
+            tma_prefetch(&maps.occ);
+            tma_prefetch(&maps.vir);
             int stage = 0;
             uint32_t phase = 0;
-            int issued[STAGES] = {};
-            uint32_t issued_phase[STAGES] = {};
+            int issued[PR_STAGES] = {};
+            uint32_t issued_phase[PR_STAGES] = {};
             bool ok = true;
-            for (int tile = blockIdx.x; tile < args.n_tiles && ok; tile += gridDim.x) {
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
                 int bp, bq;
-                tile_coords(tile, args.nb, bp, bq);
+                pair_tile(tile, args.nb, bp, bq);
                 for (int c = 0; c < chunks_per_tile; ++c) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, args.abort_flag, 1)) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, args.abort_flag, 1, TIMEOUT_NS)) {
                         ok = false;
                         break;
                     }
                     const bool occ = c < n_occ_chunks;
                     const int x = (occ ? c : c - n_occ_chunks) * BK;
-                    const CUtensorMap *mp = &maps.m[occ ? 0 : 4];
-                    unsigned char *st = smem + stage * STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
+                    const CUtensorMap *mp = occ ? &maps.occ : &maps.vir;
+                    unsigned char *st = smem + stage * PR_STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[stage], PR_STAGE_BYTES);
 #pragma unroll
                     for (int pl = 0; pl < 4; ++pl) {
-                        tma_load_2d(st + pl * PLANE_TILE, mp + pl, &full[stage], x, bp * BM);
-                        tma_load_2d(st + (4 + pl) * PLANE_TILE, mp + pl, &full[stage], x, bq * BM);
+                        tma_load_3d(st + pl * TILE_BYTES, mp, &full[stage], x, bp * 128, 4 * t + pl);
+                        tma_load_3d(st + (4 + pl) * TILE_BYTES, mp, &full[stage], x, bq * 128, 4 * t + pl);
                     }
                     issued[stage] = 1;
                     issued_phase[stage] = phase;
-                    if (++stage == STAGES) {
+                    if (++stage == PR_STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
                 }
             }
-            if (!ok) {
-                // Drain: wait (bounded) until the last copies issued into each stage have landed.
-                for (int s = 0; s < STAGES; ++s) {
-                    if (!issued[s]) continue;
-                    const unsigned long long t0 = globaltimer();
-                    while (!mbar_try_wait(&full[s], issued_phase[s]) && globaltimer() - t0 < TIMEOUT_NS) {
-                    }
-                }
-            }
+            if (!ok)
+                for (int s = 0; s < PR_STAGES; ++s)
+                    if (issued[s]) mbar_drain(&full[s], issued_phase[s], TIMEOUT_NS);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -291,15 +431,15 @@ __global__ void __launch_bounds__(THREADS, 1) pairs_mixed_kernel(const __grid_co
             int stage = 0;
             uint32_t phase = 0, tphase = 0;
             bool ok = true;
-            const uint32_t id_pos = idesc_bf16(false), id_neg = idesc_bf16(true);
-            for (int tile = blockIdx.x; tile < args.n_tiles && ok; tile += gridDim.x) {
-                if (!mbar_wait(tmem_empty, tphase ^ 1u, args.abort_flag, 2)) {
+            const uint32_t id_pos = idesc_bf16(128, false), id_neg = idesc_bf16(128, true);
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                if (!mbar_wait(tmem_empty, tphase ^ 1u, args.abort_flag, 2, TIMEOUT_NS)) {
                     ok = false;
                     break;
                 }
                 fence_after();
                 for (int c = 0; c < chunks_per_tile; ++c) {
-                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 3)) {
+                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 3, TIMEOUT_NS)) {
                         ok = false;
                         break;
                     }
@@ -309,13 +449,17 @@ __global__ void __launch_bounds__(THREADS, 1) pairs_mixed_kernel(const __grid_co
                     const int kvalid = (occ ? args.n_occ : args.n_vir) - cc * BK;
                     const int ksteps = kvalid >= BK ? BK / 16 : (kvalid + 15) / 16;
                     const uint32_t d_re = tmem + (occ ? 256u : 0u), d_im = d_re + 128u;
-                    const uint32_t base = smem_u32(smem + stage * STAGE_BYTES);
+                    const uint32_t base = smem_u32(smem + stage * PR_STAGE_BYTES);
                     for (int ks = 0; ks < ksteps; ++ks) {
-                        const uint32_t off = ks * 32;  // 16 BF16 along K
-                        const uint64_t arh = sdesc(base + 0 * PLANE_TILE + off), arl = sdesc(base + 1 * PLANE_TILE + off);
-                        const uint64_t aih = sdesc(base + 2 * PLANE_TILE + off), ail = sdesc(base + 3 * PLANE_TILE + off);
-                        const uint64_t brh = sdesc(base + 4 * PLANE_TILE + off), brl = sdesc(base + 5 * PLANE_TILE + off);
-                        const uint64_t bih = sdesc(base + 6 * PLANE_TILE + off), bil = sdesc(base + 7 * PLANE_TILE + off);
+                        const uint32_t off = ks * 32;
+                        const uint64_t arh = sdesc_sw64(base + 0 * TILE_BYTES + off);
+                        const uint64_t arl = sdesc_sw64(base + 1 * TILE_BYTES + off);
+                        const uint64_t aih = sdesc_sw64(base + 2 * TILE_BYTES + off);
+                        const uint64_t ail = sdesc_sw64(base + 3 * TILE_BYTES + off);
+                        const uint64_t brh = sdesc_sw64(base + 4 * TILE_BYTES + off);
+                        const uint64_t brl = sdesc_sw64(base + 5 * TILE_BYTES + off);
+                        const uint64_t bih = sdesc_sw64(base + 6 * TILE_BYTES + off);
+                        const uint64_t bil = sdesc_sw64(base + 7 * TILE_BYTES + off);
                         const uint32_t acc = (cc == 0 && ks == 0) ? 0u : 1u;
                         // Re G += Xr Yr^T + Xi Yi^T
                         umma(d_re, arh, brh, id_pos, acc);
@@ -333,7 +477,7 @@ __global__ void __launch_bounds__(THREADS, 1) pairs_mixed_kernel(const __grid_co
                         umma(d_im, arl, bih, id_neg, 1u);
                     }
                     umma_commit(&empty[stage]);
-                    if (++stage == STAGES) {
+                    if (++stage == PR_STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -342,148 +486,124 @@ __global__ void __launch_bounds__(THREADS, 1) pairs_mixed_kernel(const __grid_co
                 umma_commit(tmem_full);
                 tphase ^= 1u;
             }
+            umma_commit(&empty[stage]);
+            mbar_drain(&empty[stage], phase, TIMEOUT_NS);
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
+        // ---------------- epilogue (8 warps, two per lane quarter) ----------------
+        const int ew = warp - 2;
         const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+        const int qhalf = ew >> 2;     // q-pairs 8*qhalf .. +7 of the tile
         const int row = 32 * quarter + lane;
-        const int p_local = row >> 3, e = (row >> 2) & 1;
+        const int p_local = row >> 3, e = (row >> 2) & 1, c = lane & 3;
         const int gbase = lane & ~7;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
         uint32_t ephase = 0;
-        for (int tile = blockIdx.x; tile < args.n_tiles; tile += gridDim.x) {
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
             int bp, bq;
-            tile_coords(tile, args.nb, bp, bq);
-            const bool got = mbar_wait(tmem_full, ephase, args.abort_flag, 4);
-            if (epilogue_any(!got)) break;  // all four epilogue warps leave together
+            pair_tile(tile, args.nb, bp, bq);
+            const bool got = mbar_wait(tmem_full, ephase, args.abort_flag, 4, TIMEOUT_NS);
+            if (bar_any<1, 32 * PR_EPI_WARPS>(!got)) break;  // all epilogue warps leave together
             ephase ^= 1u;
             fence_after();
             const int p = bp * 16 + p_local;
-            double acc = 0.0;  // sum over q of Re f_pq a_q (valid in every lane of the group)
-            for (int ql = 0; ql < 16; ++ql) {
-                float gpr[8], gpi[8], gmr[8], gmi[8];
-                const uint32_t col = 8u * ql;
-                tmem_ld8(lane_addr + col, gpr);
-                tmem_ld8(lane_addr + 128u + col, gpi);
-                tmem_ld8(lane_addr + 256u + col, gmr);
-                tmem_ld8(lane_addr + 384u + col, gmi);
+            double acc = 0.0;  // sum over this warp's q of Re f_pq a_q
+            for (int qb = 0; qb < 4; ++qb) {
+                const int q0 = 8 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
+                float gpr[16], gpi[16], gmr[16], gmi[16];
+                const uint32_t col = 8u * q0;
+                tmem_ld<16>(lane_addr + col, gpr);
+                tmem_ld<16>(lane_addr + 128u + col, gpi);
+                tmem_ld<16>(lane_addr + 256u + col, gmr);
+                tmem_ld<16>(lane_addr + 384u + col, gmi);
                 tmem_wait_ld();
-                // This lane holds row c of: G-(xe, ye) [own], G+(xe, ye) [diag], G+(xe, y(1-e)) [off].
-                float own_r[4], own_i[4], dia_r[4], dia_i[4], off_r[4], off_i[4];
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    own_r[d] = gmr[4 * e + d];
-                    own_i[d] = gmi[4 * e + d];
-                    dia_r[d] = gpr[4 * e + d];
-                    dia_i[d] = gpi[4 * e + d];
-                    off_r[d] = gpr[4 * (1 - e) + d];
-                    off_i[d] = gpi[4 * (1 - e) + d];
-                }
-                // Direct: T_e = sum_cd conj(G-_cd) G+_cd over the like-electron block.
-                float tr = 0.f, ti = 0.f;
+                for (int qq = 0; qq < 2; ++qq) {
+                    // This lane holds row c of G-(xe, ye) [own], G+(xe, ye) [dia], G+(xe, y(1-e)) [off].
+                    float own_r[4], own_i[4], dia_r[4], dia_i[4], off_r[4], off_i[4];
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    tr += own_r[d] * dia_r[d] + own_i[d] * dia_i[d];
-                    ti += own_r[d] * dia_i[d] - own_i[d] * dia_r[d];
-                }
-                tr += __shfl_xor_sync(0xffffffffu, tr, 1);
-                ti += __shfl_xor_sync(0xffffffffu, ti, 1);
-                tr += __shfl_xor_sync(0xffffffffu, tr, 2);
-                ti += __shfl_xor_sync(0xffffffffu, ti, 2);
-                const float ur = __shfl_xor_sync(0xffffffffu, tr, 4);
-                const float ui = __shfl_xor_sync(0xffffffffu, ti, 4);
-                const float direct_re = tr * ur - ti * ui;
-                // Exchange: tr[G-(1q,1p) G+(1p,2q) G-(2q,2p) G+(2p,1q)] = sum_{c,c''} U_{cc''} V_{c''c}
-                // with U = G+(1p,2q) G-(2p,2q)^dag and V = G+(2p,1q) G-(1p,1q)^dag.  Lane (e, c)
-                // pairs its rows with those of lane (1-e, c'') received by shuffle; e = 0 lanes
-                // take c'' - c = 0, 1 and e = 1 lanes c'' - c = 2, 3 (mod 4).
-                float xr = 0.f;
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const int c = lane & 3;
-                    const int src = gbase + (e == 0 ? 4 + ((c + s) & 3) : ((c + 2 - s) & 3));
-                    float rg_r[4], rg_i[4], ro_r[4], ro_i[4];
+                    for (int d = 0; d < 4; ++d) {  // constant indices keep the arrays in registers
+                        const int i0 = 8 * qq + d, i1 = 8 * qq + 4 + d;
+                        own_r[d] = e ? gmr[i1] : gmr[i0];
+                        own_i[d] = e ? gmi[i1] : gmi[i0];
+                        dia_r[d] = e ? gpr[i1] : gpr[i0];
+                        dia_i[d] = e ? gpi[i1] : gpi[i0];
+                        off_r[d] = e ? gpr[i0] : gpr[i1];
+                        off_i[d] = e ? gpi[i0] : gpi[i1];
+                    }
+                    // Direct: T_e = sum_cd conj(G-_cd) G+_cd over the like-electron block.
+                    float tr = 0.f, ti = 0.f;
 #pragma unroll
                     for (int d = 0; d < 4; ++d) {
-                        rg_r[d] = __shfl_sync(0xffffffffu, own_r[d], src);
-                        rg_i[d] = __shfl_sync(0xffffffffu, own_i[d], src);
-                        ro_r[d] = __shfl_sync(0xffffffffu, off_r[d], src);
-                        ro_i[d] = __shfl_sync(0xffffffffu, off_i[d], src);
+                        tr += own_r[d] * dia_r[d] + own_i[d] * dia_i[d];
+                        ti += own_r[d] * dia_i[d] - own_i[d] * dia_r[d];
                     }
-                    // A1 = sum_b own_off[b] conj(recv_own[b]); A2 = sum_a recv_off[a] conj(own[a])
-                    float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
+                    tr += __shfl_xor_sync(0xffffffffu, tr, 1);
+                    ti += __shfl_xor_sync(0xffffffffu, ti, 1);
+                    tr += __shfl_xor_sync(0xffffffffu, tr, 2);
+                    ti += __shfl_xor_sync(0xffffffffu, ti, 2);
+                    const float ur = __shfl_xor_sync(0xffffffffu, tr, 4);
+                    const float ui = __shfl_xor_sync(0xffffffffu, ti, 4);
+                    const float direct_re = tr * ur - ti * ui;
+                    // Exchange: tr[G-(1q,1p) G+(1p,2q) G-(2q,2p) G+(2p,1q)] = sum_{c,c''} U_{cc''} V_{c''c},
+                    // U = G+(1p,2q) G-(2p,2q)^dag, V = G+(2p,1q) G-(1p,1q)^dag.  Lane (e, c) pairs its
+                    // rows with lane (1-e, c''): e = 0 takes c'' - c = 0, 1 and e = 1 takes 2, 3 (mod 4).
+                    float xr = 0.f;
 #pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        a1r += off_r[d] * rg_r[d] + off_i[d] * rg_i[d];
-                        a1i += off_i[d] * rg_r[d] - off_r[d] * rg_i[d];
-                        a2r += ro_r[d] * own_r[d] + ro_i[d] * own_i[d];
-                        a2i += ro_i[d] * own_r[d] - ro_r[d] * own_i[d];
+                    for (int s = 0; s < 2; ++s) {
+                        const int src = gbase + (e == 0 ? 4 + ((c + s) & 3) : ((c + 2 - s) & 3));
+                        float rg_r[4], rg_i[4], ro_r[4], ro_i[4];
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) {
+                            rg_r[d] = __shfl_sync(0xffffffffu, own_r[d], src);
+                            rg_i[d] = __shfl_sync(0xffffffffu, own_i[d], src);
+                            ro_r[d] = __shfl_sync(0xffffffffu, off_r[d], src);
+                            ro_i[d] = __shfl_sync(0xffffffffu, off_i[d], src);
+                        }
+                        float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) {
+                            a1r += off_r[d] * rg_r[d] + off_i[d] * rg_i[d];
+                            a1i += off_i[d] * rg_r[d] - off_r[d] * rg_i[d];
+                            a2r += ro_r[d] * own_r[d] + ro_i[d] * own_i[d];
+                            a2i += ro_i[d] * own_r[d] - ro_r[d] * own_i[d];
+                        }
+                        xr += a1r * a2r - a1i * a2i;
                     }
-                    xr += a1r * a2r - a1i * a2i;
+                    xr += __shfl_xor_sync(0xffffffffu, xr, 1);
+                    xr += __shfl_xor_sync(0xffffffffu, xr, 2);
+                    xr += __shfl_xor_sync(0xffffffffu, xr, 4);
+                    const int ql = q0 + qq;
+                    const int q = bq * 16 + ql;
+                    const bool valid = p < args.m && q < args.m && (bp < bq || p_local < ql);
+                    if (valid) acc += (double)(-0.5f * (direct_re - xr)) * args.a[q];
                 }
-                xr += __shfl_xor_sync(0xffffffffu, xr, 1);
-                xr += __shfl_xor_sync(0xffffffffu, xr, 2);
-                xr += __shfl_xor_sync(0xffffffffu, xr, 4);
-                const int q = bq * 16 + ql;
-                const bool valid = p < args.m && q < args.m && (bp < bq || p_local < ql);
-                if (valid) acc += (double)(-0.5f * (direct_re - xr)) * args.a[q];
             }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tmem_empty);
-            // Per-pair sums: lane 8j of the warp holds pair p_local = 4 quarter + j.
-            if ((lane & 7) == 0) red[4 * quarter + (lane >> 3)] = (p < args.m) ? acc * args.a[p] : 0.0;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (warp == 2 && lane == 0) {
+            if ((lane & 7) == 0) red[16 * qhalf + 4 * quarter + (lane >> 3)] = (p < args.m) ? acc * args.a[p] : 0.0;
+            bar_sync<1, 32 * PR_EPI_WARPS>();
+            if (ew == 0 && lane == 0) {
                 double sum = 0.0;
-                for (int j = 0; j < 16; ++j) sum += red[j];
-                args.partials[(size_t)args.t_index * args.n_tiles + tile] = sum * args.inv_lambda;
+                for (int j = 0; j < 32; ++j) sum += red[j];
+                args.partials[(size_t)t * args.n_tiles + tile] = sum * args.inv_lambda;
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            bar_sync<1, 32 * PR_EPI_WARPS>();
         }
     }
     fence_before();
     __syncthreads();
     if (warp == 1) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        tmem_dealloc(tmem, PR_TMEM_COLS);
     }
 }
 
-// Scale and split: plane[pl][row][k] for the occupied (k < n_occ) or virtual block,
-// X = phi * s_k(tau) in FP32, hi = bf16(X), lo = bf16(X - hi).
-__global__ void scale_split_kernel(const float2 *__restrict__ phi, const double *__restrict__ scale, int rows,
-                                   int n_occ, int n_vir, int k_occ_pad, int k_vir_pad, __nv_bfloat16 *occ_planes,
-                                   __nv_bfloat16 *vir_planes)
-{
-    const int n_orb = n_occ + n_vir;
-    const int row = blockIdx.y;
-    const size_t occ_plane = (size_t)rows * k_occ_pad, vir_plane = (size_t)rows * k_vir_pad;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_orb; k += gridDim.x * blockDim.x) {
-        const float2 v = phi[(size_t)row * n_orb + k];
-        const float s = (float)scale[k];
-        const float xr = v.x * s, xi = v.y * s;
-        const __nv_bfloat16 rh = __float2bfloat16_rn(xr), ih = __float2bfloat16_rn(xi);
-        const __nv_bfloat16 rl = __float2bfloat16_rn(xr - __bfloat162float(rh));
-        const __nv_bfloat16 il = __float2bfloat16_rn(xi - __bfloat162float(ih));
-        __nv_bfloat16 *base;
-        size_t plane, idx;
-        if (k < n_occ) {
-            base = occ_planes;
-            plane = occ_plane;
-            idx = (size_t)row * k_occ_pad + k;
-        } else {
-            base = vir_planes;
-            plane = vir_plane;
-            idx = (size_t)row * k_vir_pad + (k - n_occ);
-        }
-        base[idx] = rh;
-        base[plane + idx] = rl;
-        base[2 * plane + idx] = ih;
-        base[3 * plane + idx] = il;
-    }
-}
-
+// ===========================================================================
+// Host side
+// ===========================================================================
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -499,71 +619,170 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+int round8(int x) { return (x + 7) / 8 * 8; }
 
-}  // namespace
-
-MixedLayout mixed_layout(int m, int n_occ, int n_vir, size_t offset)
+uint16_t f2bf(float f)  // round to nearest even (finite inputs)
 {
-    MixedLayout L{};
-    L.k_occ_pad = (n_occ + 7) / 8 * 8;
-    L.k_vir_pad = (n_vir + 7) / 8 * 8;
-    L.rows = 8 * m;
-    L.rows_pad = L.rows;
-    L.planes = align256(offset);
-    L.planes_bytes = (size_t)4 * L.rows * (L.k_occ_pad + L.k_vir_pad) * 2;
-    L.end = align256(L.planes + L.planes_bytes) + 256;  // + the time-out flag word
-    return L;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
 }
 
-int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, std::string &err)
+float bf2f(uint16_t h)
 {
-    plan.ready = false;
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// 2-D (or 3-D) BF16 tensor map with 64-byte swizzle and a 32 x 128 box.
+int encode(void *out, void *addr, int rank, const cuuint64_t *dims, const cuuint64_t *strides, std::string &err)
+{
     auto enc = encode_fn();
     if (!enc) {
         err = "cuTensorMapEncodeTiled is not available from the driver";
         return MCMP2_EUNSUPPORTED;
     }
-    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
-    char *occ = ws + L.planes;
-    char *vir = occ + (size_t)4 * L.rows * L.k_occ_pad * 2;
-    for (int blk = 0; blk < 2; ++blk) {
-        const int kv = blk == 0 ? s.n_occ : s.n_vir;
-        const int kp = blk == 0 ? L.k_occ_pad : L.k_vir_pad;
-        char *base = blk == 0 ? occ : vir;
-        for (int pl = 0; pl < 4; ++pl) {
-            CUtensorMap map;
-            const cuuint64_t dims[2] = {(cuuint64_t)kv, (cuuint64_t)L.rows};
-            const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-            const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
-            const cuuint32_t estr[2] = {1, 1};
-            void *addr = base + (size_t)pl * L.rows * kp * 2;
-            const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, addr, dims, strides, box, estr,
-                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) {
-                err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
-                return MCMP2_ECUDA;
-            }
-            std::memcpy(plan.tmap[blk * 4 + pl], &map, sizeof(map));
-        }
-    }
-    plan.flag_off = align256(L.planes + L.planes_bytes);
-    if (cudaMemset(ws + plan.flag_off, 0, sizeof(int)) != cudaSuccess) {
-        err = "cudaMemset of the time-out flag failed";
+    const cuuint32_t box[3] = {(cuuint32_t)BK, 128u, 1u};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap map;
+    const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, addr, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
         return MCMP2_ECUDA;
     }
-    if (cudaFuncSetAttribute(pairs_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-        cudaSuccess) {
-        err = "cannot reserve shared memory for the tensor-core kernel";
+    std::memcpy(out, &map, sizeof(map));
+    return MCMP2_OK;
+}
+
+}  // namespace
+
+MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t offset)
+{
+    MixedLayout L{};
+    L.nl = n_l;
+    L.nl_pad = round8(n_l);
+    L.nl3_pad = round8(3 * n_l);
+    L.n_kb_occ = (n_occ + 63) / 64;
+    L.n_kb_vir = (n_vir + 63) / 64;
+    L.n_kb = L.n_kb_occ + L.n_kb_vir;
+    L.wt_rows = 2 * L.n_kb * 128;
+    L.P = 2 * m;
+    L.rows = 8 * m;
+    L.k_occ_pad = round8(n_occ);
+    L.k_vir_pad = round8(n_vir);
+    L.n_tau = n_tau;
+    size_t off = align256(offset);
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.BL_hi = take((size_t)L.P * L.nl_pad * 2);
+    L.BL_lo = take((size_t)L.P * L.nl_pad * 2);
+    L.BS_hi = take((size_t)L.P * L.nl3_pad * 2);
+    L.BS_lo = take((size_t)L.P * L.nl3_pad * 2);
+    L.WTL_hi = take((size_t)L.wt_rows * L.nl_pad * 2);
+    L.WTL_lo = take((size_t)L.wt_rows * L.nl_pad * 2);
+    L.WTS_hi = take((size_t)L.wt_rows * L.nl3_pad * 2);
+    L.WTS_lo = take((size_t)L.wt_rows * L.nl3_pad * 2);
+    L.occ_planes = take((size_t)n_tau * 4 * L.rows * L.k_occ_pad * 2);
+    L.vir_planes = take((size_t)n_tau * 4 * L.rows * L.k_vir_pad * 2);
+    L.flag = take(sizeof(int));
+    L.end = off;
+    return L;
+}
+
+int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *WL,
+                  const double *WS, cudaStream_t st, std::string &err)
+{
+    plan.ready = false;
+    const int nl = s.n_l, no = s.n_orb;
+    // Transposed coefficient planes: row (c, kb, ri, kk) of component c, 64-orbital block kb
+    // (occupied blocks first), real/imaginary part ri, orbital kk of the block; column = basis index.
+    std::vector<uint16_t> lh((size_t)L.wt_rows * L.nl_pad, 0), ll(lh.size(), 0);
+    std::vector<uint16_t> sh((size_t)L.wt_rows * L.nl3_pad, 0), sl(sh.size(), 0);
+    for (int c = 0; c < 2; ++c)
+        for (int kb = 0; kb < L.n_kb; ++kb)
+            for (int ri = 0; ri < 2; ++ri)
+                for (int kk = 0; kk < 64; ++kk) {
+                    int k;
+                    if (kb < L.n_kb_occ) {
+                        k = kb * 64 + kk;
+                        if (k >= s.n_occ) continue;
+                    } else {
+                        const int kv = (kb - L.n_kb_occ) * 64 + kk;
+                        if (kv >= s.n_vir) continue;
+                        k = s.n_occ + kv;
+                    }
+                    const size_t row = ((size_t)(c * L.n_kb + kb) * 2 + ri) * 64 + kk;
+                    for (int mu = 0; mu < nl; ++mu) {
+                        const float w = (float)WL[(((size_t)mu * 2 + c) * no + k) * 2 + ri];
+                        const uint16_t h = f2bf(w);
+                        lh[row * L.nl_pad + mu] = h;
+                        ll[row * L.nl_pad + mu] = f2bf(w - bf2f(h));
+                    }
+                    for (int j = 0; j < 3; ++j)
+                        for (int mu = 0; mu < nl; ++mu) {
+                            const float w = (float)WS[((((size_t)j * nl + mu) * 2 + c) * no + k) * 2 + ri];
+                            const uint16_t h = f2bf(w);
+                            sh[row * L.nl3_pad + (size_t)j * nl + mu] = h;
+                            sl[row * L.nl3_pad + (size_t)j * nl + mu] = f2bf(w - bf2f(h));
+                        }
+                }
+    if (cudaMemcpyAsync(ws + L.WTL_hi, lh.data(), lh.size() * 2, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + L.WTL_lo, ll.data(), ll.size() * 2, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + L.WTS_hi, sh.data(), sh.size() * 2, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + L.WTS_lo, sl.data(), sl.size() * 2, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(ws + L.flag, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        err = "copying the mixed-form operands failed";
+        return MCMP2_ECUDA;
+    }
+    // Tensor maps.  Spinor formation: A = basis planes [P][K], B = transposed coefficients [wt_rows][K].
+    int rc;
+    {
+        const cuuint64_t dl[2] = {(cuuint64_t)nl, (cuuint64_t)L.P}, sl_[1] = {(cuuint64_t)L.nl_pad * 2};
+        const cuuint64_t ds[2] = {(cuuint64_t)3 * nl, (cuuint64_t)L.P}, ss_[1] = {(cuuint64_t)L.nl3_pad * 2};
+        const cuuint64_t wl[2] = {(cuuint64_t)nl, (cuuint64_t)L.wt_rows};
+        const cuuint64_t wsd[2] = {(cuuint64_t)3 * nl, (cuuint64_t)L.wt_rows};
+        if ((rc = encode(plan.maps_spinor[0], ws + L.BL_hi, 2, dl, sl_, err)) ||
+            (rc = encode(plan.maps_spinor[1], ws + L.BL_lo, 2, dl, sl_, err)) ||
+            (rc = encode(plan.maps_spinor[2], ws + L.WTL_hi, 2, wl, sl_, err)) ||
+            (rc = encode(plan.maps_spinor[3], ws + L.WTL_lo, 2, wl, sl_, err)) ||
+            (rc = encode(plan.maps_spinor[4], ws + L.BS_hi, 2, ds, ss_, err)) ||
+            (rc = encode(plan.maps_spinor[5], ws + L.BS_lo, 2, ds, ss_, err)) ||
+            (rc = encode(plan.maps_spinor[6], ws + L.WTS_hi, 2, wsd, ss_, err)) ||
+            (rc = encode(plan.maps_spinor[7], ws + L.WTS_lo, 2, wsd, ss_, err)))
+            return rc;
+    }
+    // Contraction: planes [4 n_tau][rows][k_pad] as a 3-D tensor (orbital, row, 4 tau + plane).
+    {
+        const cuuint64_t dO[3] = {(cuuint64_t)s.n_occ, (cuuint64_t)L.rows, (cuuint64_t)4 * L.n_tau};
+        const cuuint64_t sO[2] = {(cuuint64_t)L.k_occ_pad * 2, (cuuint64_t)L.rows * L.k_occ_pad * 2};
+        const cuuint64_t dV[3] = {(cuuint64_t)s.n_vir, (cuuint64_t)L.rows, (cuuint64_t)4 * L.n_tau};
+        const cuuint64_t sV[2] = {(cuuint64_t)L.k_vir_pad * 2, (cuuint64_t)L.rows * L.k_vir_pad * 2};
+        if ((rc = encode(plan.maps_pairs[0], ws + L.occ_planes, 3, dO, sO, err)) ||
+            (rc = encode(plan.maps_pairs[1], ws + L.vir_planes, 3, dV, sV, err)))
+            return rc;
+    }
+    if (cudaFuncSetAttribute(spinor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
+            cudaSuccess) {
+        err = "cannot reserve shared memory for the tensor-core kernels";
         return MCMP2_ECUDA;
     }
     plan.ready = true;
     return MCMP2_OK;
 }
 
-int mixed_pairs(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const float *phi,
-                const double *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
-                cudaEvent_t *ev, int *n_launches, int *n_pair_launches)
+int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *r,
+               const double *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
+               cudaEvent_t *ev, int *n_launches, int *n_pair_launches)
 {
     if (!plan.ready) {
         err = "mixed path not prepared";
@@ -572,49 +791,52 @@ int mixed_pairs(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int *flag = reinterpret_cast<int *>(ws + L.flag);
+    auto bf = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(ws + off); };
+
+    dim3 gb((s.n_l + 127) / 128, L.P);
+    basis_split_kernel<<<gb, 128, 0, st>>>(s, r, bf(L.BL_hi), bf(L.BL_lo), bf(L.BS_hi), bf(L.BS_lo), L.nl_pad,
+                                           L.nl3_pad);
+
+    SpinorMaps smaps;
+    std::memcpy(&smaps, plan.maps_spinor, sizeof(smaps));
+    const int n_mt = (L.P + 127) / 128;
+    SpinorArgs sa{scale, bf(L.occ_planes), bf(L.vir_planes), flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ,
+                  s.n_occ, s.n_vir, s.n_orb, s.n_tau, L.rows, L.k_occ_pad, L.k_vir_pad};
+    const int sp_tiles = n_mt * 4 * L.n_kb;
+    spinor_mixed_kernel<<<sp_tiles < sms ? sp_tiles : sms, SP_THREADS, SP_SMEM, st>>>(smaps, sa);
+
+    PairMaps pmaps;
+    std::memcpy(&pmaps.occ, plan.maps_pairs[0], sizeof(CUtensorMap));
+    std::memcpy(&pmaps.vir, plan.maps_pairs[1], sizeof(CUtensorMap));
     const int nb = pair_blocks(s.m, 16);
     const int n_tiles = nb * (nb + 1) / 2;
-    MixedMaps maps;
-    std::memcpy(&maps, plan.tmap, sizeof(maps));
-    __nv_bfloat16 *occ = reinterpret_cast<__nv_bfloat16 *>(ws + L.planes);
-    __nv_bfloat16 *vir = occ + (size_t)4 * L.rows * L.k_occ_pad;
-    int *flag = reinterpret_cast<int *>(ws + plan.flag_off);
-    MixedArgs args{a, partials, flag, s.m, n_tiles, nb, 0, s.n_occ, s.n_vir, 1.0 / s.lambda};
-    const int grid = n_tiles < sms ? n_tiles : sms;
-    int launches = 0, pair_launches = 0;
-    for (int t = 0; t < s.n_tau; ++t) {
-        dim3 g((s.n_orb + 255) / 256, L.rows);
-        scale_split_kernel<<<g, 256, 0, st>>>(reinterpret_cast<const float2 *>(phi), scale + (size_t)t * s.n_orb, L.rows,
-                                              s.n_occ, s.n_vir, L.k_occ_pad, L.k_vir_pad, occ, vir);
-        ++launches;
-        if (ev) cudaEventRecord(ev[2 * t], st);
-        args.t_index = t;
-        pairs_mixed_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(maps, args);
-        if (ev) cudaEventRecord(ev[2 * t + 1], st);
-        ++launches;
-        ++pair_launches;
-    }
+    PairArgs pa{a, partials, flag, s.m, n_tiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda};
+    const int items = n_tiles * s.n_tau;
+    if (ev) cudaEventRecord(ev[0], st);
+    pairs_mixed_kernel<<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+    if (ev) cudaEventRecord(ev[1], st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
-        err = std::string("tensor-core contraction launch: ") + cudaGetErrorString(e);
+        err = std::string("mixed-form launch: ") + cudaGetErrorString(e);
         return MCMP2_ECUDA;
     }
-    if (n_launches) *n_launches = launches;
-    if (n_pair_launches) *n_pair_launches = pair_launches;
+    if (n_launches) *n_launches = 3;
+    if (n_pair_launches) *n_pair_launches = 1;
     return MCMP2_OK;
 }
 
-int mixed_check_flag(MixedPlan &plan, char *ws, cudaStream_t st, std::string &err)
+int mixed_check_flag(const MixedLayout &L, char *ws, cudaStream_t st, std::string &err)
 {
     int h = 0;
-    if (cudaMemcpyAsync(&h, ws + plan.flag_off, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(&h, ws + L.flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         err = "cannot read the time-out flag";
         return MCMP2_ECUDA;
     }
     if (h != 0) {
-        err = "tensor-core contraction timed out waiting (role " + std::to_string(h) + ")";
-        cudaMemsetAsync(ws + plan.flag_off, 0, sizeof(int), st);
+        err = "tensor-core kernel timed out waiting (role " + std::to_string(h) + ")";
+        cudaMemsetAsync(ws + L.flag, 0, sizeof(int), st);
         return MCMP2_ETIMEOUT;
     }
     return MCMP2_OK;

@@ -1,9 +1,12 @@
 // Step reduction and blocking statistics: I'_n of Eq. redundant from the
 // per-tile partial sums, and the Flyvbjerg-Petersen accumulators of
 // Eq. uncertainty, in FP64 with compensated sums and a fixed summation order.
+#include "../../include/mcmp2.h"
 #include "internal.cuh"
 
 namespace mcmp2 {
+
+constexpr int MCMP2_BLOCK = MCMP2_BLOCK_SIZE;
 
 __device__ __forceinline__ void kahan_add(double &s, double &c, double x)
 {
@@ -13,25 +16,43 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double x)
     s = t;
 }
 
-// One block of 256 threads.  partials: [n_tau][n_tiles].
-__global__ void __launch_bounds__(256) reduce_kernel(int n_tau, int m, const double *__restrict__ partials,
-                                                     int n_tiles, double *__restrict__ out_slot,
-                                                     Stats *__restrict__ st, int update,
-                                                     unsigned long long *__restrict__ step)
+// Error-free sum of two doubles: s + err == a + b exactly.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &err)
 {
-    __shared__ double sv[256], sc[256];
+    s = a + b;
+    const double bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+
+constexpr int RED_THREADS = 512;
+
+// One block.  partials: [n_tau][n_tiles].  Each thread forms a compensated sum
+// of a strided slice, then a fixed pairwise tree combines the (sum, error)
+// pairs with error-free additions, so the result is deterministic and carries
+// the compensation of every level.
+__global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, const double *__restrict__ partials,
+                                                             int n_tiles, double *__restrict__ out_slot,
+                                                             Stats *__restrict__ st, int update,
+                                                             unsigned long long *__restrict__ step)
+{
+    __shared__ double sv[RED_THREADS], se[RED_THREADS];
     const int total = n_tau * n_tiles;
     double s = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < total; i += 256) kahan_add(s, c, partials[i]);
+    for (int i = threadIdx.x; i < total; i += RED_THREADS) kahan_add(s, c, partials[i]);
     sv[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
+    se[threadIdx.x] = -c;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double S = 0.0, C = 0.0;
-    for (int i = 0; i < 256; ++i) {
-        kahan_add(S, C, sv[i]);
-        kahan_add(S, C, -sc[i]);
+    for (int stride = RED_THREADS / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) {
+            double sum, err;
+            two_sum(sv[threadIdx.x], sv[threadIdx.x + stride], sum, err);
+            sv[threadIdx.x] = sum;
+            se[threadIdx.x] += se[threadIdx.x + stride] + err;
+        }
+        __syncthreads();
     }
+    if (threadIdx.x != 0) return;
+    const double S = sv[0] + se[0];
     const double npairs = 0.5 * (double)m * (double)(m - 1);
     const double value = S / npairs / (double)n_tau;
     *out_slot = value;
@@ -41,8 +62,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(int n_tau, int m, const dou
         kahan_add(st->all_sum, st->all_comp, value);
         kahan_add(st->block_sum, st->block_comp, value);
         st->in_block += 1;
-        if (st->in_block == 100) {  // N_b = 100 (Sec. IV)
-            const double bm = st->block_sum / 100.0;
+        if (st->in_block == MCMP2_BLOCK) {  // N_b = 100 (Sec. IV)
+            const double bm = st->block_sum / (double)MCMP2_BLOCK;
             st->n_blocks += 1;
             const double d = bm - st->mean;
             st->mean += d / (double)st->n_blocks;
@@ -59,7 +80,7 @@ cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tile
                           Stats *stats, int update_stats, unsigned long long *step_to_advance,
                           cudaStream_t st)
 {
-    reduce_kernel<<<1, 256, 0, st>>>(s.n_tau, s.m, partials, n_tiles, out_slot, stats, update_stats,
+    reduce_kernel<<<1, RED_THREADS, 0, st>>>(s.n_tau, s.m, partials, n_tiles, out_slot, stats, update_stats,
                                      step_to_advance);
     return cudaGetLastError();
 }

@@ -100,14 +100,14 @@ cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long
                               uint64_t seed, double delta, unsigned long long *accepted,
                               cudaStream_t st)
 {
-    const int threads = 128;
+    const int threads = 32;  // FP64 exp-bound: spread the pairs over as many SMs as possible
     metropolis_kernel<<<(s.m + threads - 1) / threads, threads, 0, st>>>(s, r, step, seed, delta, accepted);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, cudaStream_t st)
 {
-    const int threads = 128;
+    const int threads = 32;
     pair_weights_kernel<<<(s.m + threads - 1) / threads, threads, 0, st>>>(s, r, a);
     return cudaGetLastError();
 }

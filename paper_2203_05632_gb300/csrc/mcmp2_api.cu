@@ -22,7 +22,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Offsets of every array inside the caller's workspace.
 struct Layout {
-    size_t centres, wcoef, shell_centre, shell_alpha, shell_coef, fn_shell, fn_pow, eps, WL, WS, WLf, WSf;
+    size_t centres, wcoef, shell_centre, shell_alpha, shell_coef, fn_shell, fn_pow, eps, WL, WS;
     size_t r, a, tau, scale, step, burn_acc, stats, per_step, stage_r, stage_tau;
     size_t B, phi, partials;
     MixedLayout mixed;
@@ -73,11 +73,7 @@ Layout make_layout(const mcmp2_dims &d, int precision)
         L.phi = take(8 * m * no * 16);
     } else {
         L.tile_pairs = TILE_PAIRS_MIXED;
-        L.WLf = take(nl * 4 * no * 4);
-        L.WSf = take(3 * nl * 4 * no * 4);
-        L.B = take(2 * m * 4 * nl * 4);
-        L.phi = take(8 * m * no * 8);
-        L.mixed = mixed_layout(d.m, d.n_occ, d.n_vir, off);
+        L.mixed = mixed_layout(d.m, d.n_functions, d.n_occ, d.n_vir, d.n_tau, off);
         off = align256(L.mixed.end);
     }
     L.n_tiles = n_tiles_for(d.m, L.tile_pairs);
@@ -342,12 +338,6 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     CK(h2d(L.eps, eps, sizeof(double) * no), "copy eps");
     CK(h2d(L.WL, WL.data(), sizeof(double) * WL.size()), "copy WL");
     CK(h2d(L.WS, WS.data(), sizeof(double) * WS.size()), "copy WS");
-    if (ctx->precision == MCMP2_MIXED) {
-        std::vector<float> WLf(WL.begin(), WL.end()), WSf(WS.begin(), WS.end());
-        CK(h2d(L.WLf, WLf.data(), sizeof(float) * WLf.size()), "copy WLf");
-        CK(h2d(L.WSf, WSf.data(), sizeof(float) * WSf.size()), "copy WSf");
-        CK(cudaStreamSynchronize(st), "load sync");
-    }
     CK(cudaStreamSynchronize(st), "load sync");
 
     DevSystem &S = ctx->sys;
@@ -373,8 +363,6 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     S.Ng = Ng;
     S.WL = ctx->at<double>(L.WL);
     S.WS = ctx->at<double>(L.WS);
-    S.WLf = ctx->precision == MCMP2_MIXED ? ctx->at<float>(L.WLf) : nullptr;
-    S.WSf = ctx->precision == MCMP2_MIXED ? ctx->at<float>(L.WSf) : nullptr;
 
     uint64_t h = 1469598103934665603ull;
     h = fnv1a(h, b->centres, sizeof(double) * 3 * b->n_centres);
@@ -389,7 +377,7 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     ctx->loaded = true;
     ctx->walkers = false;
     if (ctx->precision == MCMP2_MIXED) {
-        const int rc = mixed_prepare(ctx->mixed, S, L.mixed, ctx->ws, ctx->err);
+        const int rc = mixed_prepare(ctx->mixed, S, L.mixed, ctx->ws, WL.data(), WS.data(), st, ctx->err);
         if (rc != MCMP2_OK) {
             ctx->loaded = false;
             return rc;
@@ -424,19 +412,13 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
     CK(launch_pair_weights(S, r, a, st), "pair weights");
     CK(launch_times(S, step, seed, tau_given, tau, scale, st), "imaginary times");
     ctx->launches += 2;
-    const int n_ev = ctx->precision == MCMP2_FP64 ? 1 : S.n_tau;
-    std::vector<cudaEvent_t> ev;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     if (ctx->timing) {
-        for (int i = 0; i < n_ev; ++i) {
-            cudaEvent_t e0, e1;
-            CK(cudaEventCreate(&e0), "event");
-            CK(cudaEventCreate(&e1), "event");
-            ctx->pair_events.emplace_back(e0, e1);
-            ev.push_back(e0);
-            ev.push_back(e1);
-        }
+        CK(cudaEventCreate(&ev[0]), "event");
+        CK(cudaEventCreate(&ev[1]), "event");
+        ctx->pair_events.emplace_back(ev[0], ev[1]);
     }
-    cudaEvent_t e0 = ev.empty() ? nullptr : ev[0], e1 = ev.empty() ? nullptr : ev[1];
+    cudaEvent_t e0 = ev[0], e1 = ev[1];
     if (ctx->precision == MCMP2_FP64) {
         double *B = ctx->at<double>(L.B);
         double *phi = ctx->at<double>(L.phi);
@@ -448,15 +430,11 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         ctx->launches += 4;
         ctx->pair_launches += 1;
     } else {
-        float *B = ctx->at<float>(L.B);
-        float *phi = ctx->at<float>(L.phi);
-        CK(launch_basis<float>(S, r, B, st), "basis values");
-        CK(launch_spinors_f32(S, B, phi, st), "spinor formation");
         int n_launch = 0, n_pair = 0;
-        const int rc = mixed_pairs(ctx->mixed, S, L.mixed, ctx->ws, phi, scale, a, partials, st, ctx->err,
-                                   ev.empty() ? nullptr : ev.data(), &n_launch, &n_pair);
+        const int rc = mixed_step(ctx->mixed, S, L.mixed, ctx->ws, r, scale, a, partials, st, ctx->err,
+                                  ctx->timing ? ev : nullptr, &n_launch, &n_pair);
         if (rc != MCMP2_OK) return rc;
-        ctx->launches += 3 + n_launch;
+        ctx->launches += n_launch;
         ctx->pair_launches += n_pair;
     }
     CK(launch_reduce(S, partials, L.n_tiles, out_slot, ctx->at<Stats>(L.stats), update, advance ? step : nullptr,
@@ -552,7 +530,7 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
             return ctx->fail(MCMP2_ENONFINITE, "a step estimate is not finite");
     }
     if (ctx->precision == MCMP2_MIXED && out) {
-        const int rc = mixed_check_flag(ctx->mixed, ctx->ws, st, ctx->err);
+        const int rc = mixed_check_flag(ctx->L.mixed, ctx->ws, st, ctx->err);
         if (rc) return rc;
     }
     return MCMP2_OK;
@@ -587,7 +565,7 @@ int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const doub
         CK(cudaStreamSynchronize(st), "replay sync");
     }
     if (ctx->precision == MCMP2_MIXED) {
-        const int rc = mixed_check_flag(ctx->mixed, ctx->ws, st, ctx->err);
+        const int rc = mixed_check_flag(ctx->L.mixed, ctx->ws, st, ctx->err);
         if (rc) return rc;
     }
     for (int64_t i = 0; i < n; ++i)

@@ -1,4 +1,4 @@
-// Mixed-precision form of the propagator contraction (tensor cores).
+// Mixed-precision form of the integrand engine (tensor cores).
 #pragma once
 
 #include <string>
@@ -9,32 +9,41 @@ namespace mcmp2 {
 
 // Workspace regions of the mixed form (offsets into the caller's workspace).
 struct MixedLayout {
-    size_t planes;      // split-BF16 operand planes of one tau: occupied then virtual
-    size_t planes_bytes;
-    int k_occ_pad, k_vir_pad;  // orbital counts padded to the 16-byte TMA row granule
-    int rows, rows_pad;        // 8 m position-component rows, padded to the 128-row tile
+    int nl, nl_pad, nl3_pad;         // basis functions; padded row lengths of the value / gradient planes
+    int n_kb_occ, n_kb_vir, n_kb;    // 64-orbital blocks (occupied, virtual, total)
+    int wt_rows;                     // rows of a transposed coefficient plane: 2 components x n_kb x 128
+    int P, rows, k_occ_pad, k_vir_pad, n_tau;
+    size_t BL_hi, BL_lo, BS_hi, BS_lo;      // basis values / gradients, BF16 hi/lo: [P][nl_pad], [P][nl3_pad]
+    size_t WTL_hi, WTL_lo, WTS_hi, WTS_lo;  // transposed spinor coefficients, BF16 hi/lo: [wt_rows][nl(3)_pad]
+    size_t occ_planes, vir_planes;          // X planes of all times: [n_tau][4][rows][k_pad]
+    size_t flag;                            // time-out flag word
     size_t end;
 };
 
-// Host-side state of the mixed form (tensor maps and a launch flag buffer).
+// Host-side state: tensor maps (8 for spinor formation, 2 for the contraction).
 struct MixedPlan {
     bool ready = false;
-    alignas(64) unsigned char tmap[8][128];  // CUtensorMap objects: {occ, vir} x {re_hi, re_lo, im_hi, im_lo}
-    size_t flag_off = 0;                      // device word recording a kernel time-out
+    alignas(64) unsigned char maps_spinor[8][128];
+    alignas(64) unsigned char maps_pairs[2][128];
 };
 
-MixedLayout mixed_layout(int m, int n_occ, int n_vir, size_t offset);
-int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, std::string &err);
-// Issues the mixed-form contraction of one step (all n_tau times); if ev is
-// non-null, records ev[2t], ev[2t+1] around the contraction launch of time t;
-// reports the launches it made.
-int mixed_pairs(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const float *phi,
-                const double *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
-                cudaEvent_t *ev, int *n_launches, int *n_pair_launches);
-// Reads (synchronously) and clears the device flag a timed-out contraction sets.
-int mixed_check_flag(MixedPlan &plan, char *ws, cudaStream_t st, std::string &err);
-void mixed_release(MixedPlan &plan);
+MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t offset);
 
-cudaError_t launch_spinors_f32(const DevSystem &s, const float *B, float *phi, cudaStream_t st);
+// Builds the transposed, split coefficient planes from the host operands
+// WL [n_l][2][n_orb] and WS [3 n_l][2][n_orb] (complex) and encodes the tensor maps.
+int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *WL_host,
+                  const double *WS_host, cudaStream_t st, std::string &err);
+
+// Issues one step of the mixed integrand engine for positions r: basis planes,
+// spinor formation with the scaled split planes of every time, and the
+// contraction writing partials [n_tau][n_tiles].  ev (if non-null) gets
+// ev[0], ev[1] recorded around the contraction launch.
+int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *r,
+               const double *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
+               cudaEvent_t *ev, int *n_launches, int *n_pair_launches);
+
+// Reads (synchronously) and clears the device flag a timed-out kernel sets.
+int mixed_check_flag(const MixedLayout &L, char *ws, cudaStream_t st, std::string &err);
+void mixed_release(MixedPlan &plan);
 
 }  // namespace mcmp2

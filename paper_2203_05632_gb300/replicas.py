@@ -1,0 +1,72 @@
+"""Independent replicas and their combination (the paper's parallel scheme).
+
+Sec. III: each processor runs its own Monte Carlo integration with a distinct
+seed and no communication; only at the end are the results of the surviving
+processors combined by a weighted average.  Runs are restartable and
+concatenable.  Here a replica is one library context (one GPU); this module
+holds the host-side bookkeeping:
+
+* ``combine`` — inverse-variance weighted mean of replica results
+  (weights 1/sigma-bar^2), with its standard error;
+* ``concatenate`` — merge the blocking statistics of two runs of one replica
+  chain (block counts add; means and squared deviations combine exactly);
+* ``gather_and_combine`` — collect every rank's result over a
+  ``torch.distributed`` process group at the end of a run and combine them.
+  Ranks that failed pass ``None`` and are left out.
+"""
+from __future__ import annotations
+
+import math
+
+
+def combine(results):
+    """Inverse-variance weighted average of replica results.
+
+    results: iterable of dicts with keys 'energy' and 'error' (sigma-bar);
+    entries that are None, or have a non-positive or non-finite error, are
+    skipped.  Returns dict(energy, error, n_replicas)."""
+    num = 0.0
+    den = 0.0
+    n = 0
+    for r in results:
+        if r is None:
+            continue
+        e, s = r.get("energy"), r.get("error")
+        if e is None or s is None or not math.isfinite(e) or not math.isfinite(s) or s <= 0.0:
+            continue
+        w = 1.0 / (s * s)
+        num += w * e
+        den += w
+        n += 1
+    if n == 0:
+        return {"energy": float("nan"), "error": float("nan"), "n_replicas": 0}
+    return {"energy": num / den, "error": math.sqrt(1.0 / den), "n_replicas": n}
+
+
+def concatenate(a, b, block_size=100):
+    """Blocking statistics of the concatenation of two runs of complete blocks.
+
+    a, b: dicts with 'energy' (I_N), 'variance' (sigma_N^2) and 'n_blocks'.
+    Means and sums of squared deviations of block means combine exactly
+    (parallel form of Welford's update)."""
+    na, nb = int(a["n_blocks"]), int(b["n_blocks"])
+    if na == 0:
+        return dict(b)
+    if nb == 0:
+        return dict(a)
+    n = na + nb
+    d = b["energy"] - a["energy"]
+    mean = a["energy"] + d * nb / n
+    m2 = a["variance"] * na + b["variance"] * nb + d * d * na * nb / n
+    var = m2 / n
+    return {"energy": mean, "variance": var, "error": math.sqrt(var) / math.sqrt(n), "n_blocks": n,
+            "steps": n * block_size}
+
+
+def gather_and_combine(result, group=None):
+    """All-gather each rank's result (a dict or None) and combine them on every rank."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, result, group=group)
+    return combine(gathered), gathered
