@@ -62,7 +62,7 @@ __global__ void basis_split_kernel(DevSystem s, const double *__restrict__ r, __
     const double *A = s.centres + 3 * s.shell_centre[sh];
     const float d[3] = {(float)(r[3 * x + 0] - A[0]), (float)(r[3 * x + 1] - A[1]), (float)(r[3 * x + 2] - A[2])};
     const float al = (float)s.shell_alpha[sh];
-    const float e = (float)s.shell_coef[sh] * __expf(-al * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    const float e = (float)s.shell_coef[sh] * expf(-al * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
     const int pw[3] = {s.fn_pow[3 * mu], s.fn_pow[3 * mu + 1], s.fn_pow[3 * mu + 2]};
     float pk[3], dk[3];
 #pragma unroll

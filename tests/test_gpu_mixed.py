@@ -8,16 +8,19 @@ import synthetic
 
 pytestmark = pytest.mark.gpu
 
-# Split BF16 x3 products carry ~2^-17 relative error per product and FP32
-# accumulation over <= 400 orbitals; the traced products of four propagator
-# blocks then agree with FP64 to ~1e-5 of their size.  Per-step estimates are
-# compared relative to max(|I'_n|, 1e-3 <|f|>) as in the FP64 tests.
+# Tolerance derived from the arithmetic of the mixed form: every real product
+# of the split BF16 x3 scheme (spinor formation and propagators) carries
+# ~2^-16 relative error, accumulated in FP32; a trace term multiplies four
+# propagator entries, so each pair-of-pairs term is off by at most ~6e-5 of its
+# absolute expansion.  A sum of terms is compared with
+#   |got - want| <= REL_MIXED |want| + ABS_MIXED sum |terms|,
+# the second part covering sums whose terms cancel.
 REL_MIXED = 2e-3
+ABS_MIXED = 1e-4
 
 
-def _rel(got, want, absmean):
-    scale = np.maximum(np.abs(want), 1e-3 * absmean)
-    return np.abs(got - want) / scale
+def _ok(got, want, abs_sum):
+    return np.abs(got - want) <= REL_MIXED * np.abs(want) + ABS_MIXED * abs_sum
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +41,7 @@ def test_mixed_replay_matches_oracle_tiny(tiny, tiny_oracle, m, n_tau):
     ctx = pkg.Context(tiny, m, n_tau, pkg.MCMP2_MIXED)
     got = ctx.eval_fixed(r, tau)
     want, absmean = tiny_oracle.eval_steps(r, tau, with_abs=True)
-    assert np.all(_rel(got, want, absmean) <= REL_MIXED), (got, want)
+    assert np.all(_ok(got, want, absmean)), (got, want)
 
 
 def test_mixed_replay_matches_oracle_medium_system(medium, medium_oracle):
@@ -48,7 +51,7 @@ def test_mixed_replay_matches_oracle_medium_system(medium, medium_oracle):
     ctx = pkg.Context(medium, m, n_tau, pkg.MCMP2_MIXED)
     got = ctx.eval_fixed(r, tau)
     want, absmean = medium_oracle.eval_steps(r, tau, with_abs=True)
-    assert np.all(_rel(got, want, absmean) <= REL_MIXED), (got, want)
+    assert np.all(_ok(got, want, absmean)), (got, want)
 
 
 def _tile_pairs(bp, bq, tp, m):
@@ -79,8 +82,7 @@ def test_mixed_full_size_sampled_tiles_match_oracle(medium, medium_oracle):
         want = vals.sum(axis=0)
         k = sum(nb - b for b in range(bp)) + (bq - bp)
         got = partials[:, k]
-        scale = np.maximum(np.abs(want), 1e-3 * np.abs(vals).sum(axis=0))
-        assert np.all(np.abs(got - want) <= REL_MIXED * scale), (bp, bq, got, want)
+        assert np.all(_ok(got, want, np.abs(vals).sum(axis=0))), (bp, bq, got, want)
 
 
 def test_mixed_agrees_with_fp64_form_within_a_fifth_of_sigma(medium):
@@ -102,7 +104,7 @@ def test_mixed_agrees_with_fp64_form_within_a_fifth_of_sigma(medium):
     assert nb == 4
     assert abs(d.mean()) < 0.2 * sb, (d.mean(), sb)
     absmean = np.abs(per[pkg.MCMP2_FP64]).mean()
-    assert np.max(np.abs(d)) < REL_MIXED * absmean
+    assert np.max(np.abs(d)) < REL_MIXED * absmean  # per step, relative to the typical step size
 
 
 def test_mixed_walk_statistics_and_checkpoint(tiny_soft):
