@@ -163,6 +163,19 @@ int mcmp2_get_walkers(mcmp2_ctx *ctx, double *r_host, double *delta_host);
 int mcmp2_debug_partials(mcmp2_ctx *ctx, double *out_host, size_t capacity, int *n_tiles,
                          int *tile_pairs);
 
+/* Gradient of the replay estimate E = (1/n) sum_n I'_n for the n given samples
+ * (common random numbers: r_host [n][m][2][3], tau_host [n][n_tau] as in
+ * mcmp2_eval_fixed) with respect to the orbital energies and the spinor
+ * coefficients of the loaded system, with lambda, eps_HOMO and eps_LUMO held
+ * at their loaded values (the density the times were drawn from does not
+ * move).  Hand-written adjoint of the propagator products and traces (the
+ * derivative of the trace form of Eq. MCMP2), back through the spinor values
+ * to eps and C.  Outputs (host): energy_host (E, may be NULL), d_eps_host
+ * [n_orb], d_C_host complex [4 n_L][n_orb] in the layout of C, as
+ * dE/dRe C + i dE/dIm C.  FP64 contexts only (MCMP2_EUNSUPPORTED otherwise). */
+int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double *tau_host, double *energy_host,
+                   double *d_eps_host, double *d_C_host);
+
 /* Launch counters and CUDA-event timing of the pair-of-pairs contraction
  * kernel (the dominant kernel), measured on the context's stream. */
 typedef struct {

@@ -71,6 +71,7 @@ SIGNATURES = {
     "mcmp2_run_steps": (_I, [_P, _I64, _U64, ctypes.POINTER(Result)]),
     "mcmp2_eval_fixed": (_I, [_P, _I64, _P, _P, _P]),
     "mcmp2_get_walkers": (_I, [_P, _P, _P]),
+    "mcmp2_backward": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
     "mcmp2_debug_partials": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mcmp2_profile": (_I, [_P, _I, ctypes.POINTER(ProfileCounters)]),
     "mcmp2_checkpoint_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
@@ -206,6 +207,31 @@ class Context:
     def eval_fixed_ptr(self, n: int, r_ptr: int, tau_ptr: int, out_ptr: int):
         """Replay from raw host pointers (e.g. pinned torch tensors)."""
         self._check(self.lib.mcmp2_eval_fixed(self.h, int(n), _P(r_ptr), _P(tau_ptr), _P(out_ptr)))
+
+    def load(self, eps=None, C=None):
+        """Reload the system with new orbital energies and/or coefficients (same basis)."""
+        import dataclasses
+        sysobj = self.system
+        if eps is not None or C is not None:
+            sysobj = dataclasses.replace(sysobj, eps=self.system.eps if eps is None else np.asarray(eps),
+                                         C=self.system.C if C is None else np.asarray(C))
+        C_ = _c(sysobj.C, np.complex128)
+        eps_ = _c(sysobj.eps, np.float64)
+        self._check(self.lib.mcmp2_load_system(self.h, ctypes.byref(self._basis), int(sysobj.n_occ),
+                                               int(sysobj.n_vir), _ptr(C_), _ptr(eps_)))
+        self.system = sysobj
+
+    def backward(self, r, tau):
+        """(E, dE/d eps, dE/dC) of the replay estimate for the given samples (FP64 contexts)."""
+        r = _c(r, np.float64)
+        tau = _c(tau, np.float64)
+        n = r.shape[0]
+        e = ctypes.c_double(0.0)
+        d_eps = np.zeros(self.system.n_occ + self.system.n_vir)
+        d_C = np.zeros((4 * self.n_l, self.system.n_occ + self.system.n_vir), dtype=np.complex128)
+        self._check(self.lib.mcmp2_backward(self.h, n, _P(r.ctypes.data), _P(tau.ctypes.data), ctypes.byref(e),
+                                            _ptr(d_eps), _ptr(d_C)))
+        return e.value, d_eps, d_C
 
     def get_walkers(self):
         r = np.zeros((self.m, 2, 3))

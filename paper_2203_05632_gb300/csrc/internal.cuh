@@ -113,6 +113,12 @@ cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi,
 cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale,
                              const double *a, double *partials, cudaStream_t st);
 
+size_t adjoint_smem_bytes();
+cudaError_t launch_adjoint_time(const DevSystem &s, const double *B, const double *phi, const double *scale,
+                                const double *tau, const double *a, int t_index, double norm, double *Ybar,
+                                double *Ys, double *partials, double *GWL, double *GWS, double *d_eps,
+                                cudaStream_t st);
+
 cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tiles, double *out_slot,
                           Stats *stats, int update_stats, unsigned long long *step_to_advance,
                           cudaStream_t st);

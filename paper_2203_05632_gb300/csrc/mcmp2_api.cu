@@ -25,6 +25,7 @@ struct Layout {
     size_t centres, wcoef, shell_centre, shell_alpha, shell_coef, fn_shell, fn_pow, eps, WL, WS;
     size_t r, a, tau, scale, step, burn_acc, stats, per_step, stage_r, stage_tau;
     size_t B, phi, partials;
+    size_t Ybar, Ys, GWL, GWS, d_eps;  // adjoint buffers (FP64 form)
     MixedLayout mixed;
     size_t total;
     int tile_pairs, n_tiles;
@@ -71,6 +72,11 @@ Layout make_layout(const mcmp2_dims &d, int precision)
         L.tile_pairs = TILE_PAIRS_F64;
         L.B = take(2 * m * 4 * nl * 8);
         L.phi = take(8 * m * no * 16);
+        L.Ybar = take(8 * m * no * 16);
+        L.Ys = take(8 * m * no * 16);
+        L.GWL = take(nl * 4 * no * 8);
+        L.GWS = take(3 * nl * 4 * no * 8);
+        L.d_eps = take(no * 8);
     } else {
         L.tile_pairs = TILE_PAIRS_MIXED;
         L.mixed = mixed_layout(d.m, d.n_functions, d.n_occ, d.n_vir, d.n_tau, off);
@@ -570,6 +576,104 @@ int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const doub
     }
     for (int64_t i = 0; i < n; ++i)
         if (!std::isfinite(out[i])) return ctx->fail(MCMP2_ENONFINITE, "step %lld is not finite", (long long)i);
+    return MCMP2_OK;
+}
+
+int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double *tau_host, double *energy_host,
+                   double *d_eps_host, double *d_C_host)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
+    if (ctx->precision != MCMP2_FP64) return ctx->fail(MCMP2_EUNSUPPORTED, "the adjoint runs in the FP64 form");
+    if (n < 1 || !r_host || !tau_host || !d_eps_host || !d_C_host) return ctx->fail(MCMP2_EINVAL, "bad backward arguments");
+    const int m = ctx->dims.m, nt = ctx->dims.n_tau;
+    if (!all_finite(r_host, (size_t)n * m * 6)) return ctx->fail(MCMP2_ENONFINITE, "non-finite position");
+    for (int64_t i = 0; i < n * nt; ++i)
+        if (!(tau_host[i] >= 0.0) || !std::isfinite(tau_host[i]))
+            return ctx->fail(MCMP2_EINVAL, "imaginary times must be finite and >= 0");
+    const Layout &L = ctx->L;
+    const DevSystem &S = ctx->sys;
+    cudaStream_t st = ctx->stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int nl = S.n_l, no = S.n_orb;
+    CK(cudaMemsetAsync(ctx->ws + L.GWL, 0, (size_t)nl * 4 * no * 8, st), "zero gradients");
+    CK(cudaMemsetAsync(ctx->ws + L.GWS, 0, (size_t)3 * nl * 4 * no * 8, st), "zero gradients");
+    CK(cudaMemsetAsync(ctx->ws + L.d_eps, 0, (size_t)no * 8, st), "zero gradients");
+    const double npairs = 0.5 * (double)m * (double)(m - 1);
+    const double norm = 1.0 / ((double)n * nt * npairs);
+    double *sr = ctx->at<double>(L.stage_r), *stau = ctx->at<double>(L.stage_tau);
+    double *slots = ctx->at<double>(L.per_step);
+    double *a = ctx->at<double>(L.a), *tau = ctx->at<double>(L.tau), *scale = ctx->at<double>(L.scale);
+    double *B = ctx->at<double>(L.B), *phi = ctx->at<double>(L.phi), *partials = ctx->at<double>(L.partials);
+    unsigned long long *step = ctx->at<unsigned long long>(L.step);
+    std::vector<double> per(n);
+    for (int64_t s0 = 0; s0 < n; s0 += REPLAY_CHUNK) {
+        const int len = (int)std::min<int64_t>(REPLAY_CHUNK, n - s0);
+        CK(cudaMemcpyAsync(sr, r_host + (size_t)s0 * m * 6, sizeof(double) * len * m * 6, cudaMemcpyHostToDevice, st),
+           "copy positions");
+        CK(cudaMemcpyAsync(stau, tau_host + (size_t)s0 * nt, sizeof(double) * len * nt, cudaMemcpyHostToDevice, st),
+           "copy times");
+        for (int j = 0; j < len; ++j) {
+            const double *rj = sr + (size_t)j * m * 6;
+            CK(launch_pair_weights(S, rj, a, st), "pair weights");
+            CK(launch_times(S, step, 0, stau + (size_t)j * nt, tau, scale, st), "imaginary times");
+            CK(launch_basis<double>(S, rj, B, st), "basis values");
+            CK(launch_spinors_f64(S, B, phi, st), "spinor formation");
+            for (int t = 0; t < nt; ++t) {
+                CK(cudaMemsetAsync(ctx->ws + L.Ybar, 0, (size_t)8 * m * no * 16, st), "zero adjoint");
+                CK(launch_adjoint_time(S, B, phi, scale, tau, a, t, norm, ctx->at<double>(L.Ybar), ctx->at<double>(L.Ys),
+                                       partials, ctx->at<double>(L.GWL), ctx->at<double>(L.GWS),
+                                       ctx->at<double>(L.d_eps), st),
+                   "adjoint");
+            }
+            CK(launch_reduce(S, partials, L.n_tiles, slots + j, ctx->at<Stats>(L.stats), 0, nullptr, st), "reduce");
+        }
+        CK(cudaMemcpyAsync(per.data() + s0, slots, sizeof(double) * len, cudaMemcpyDeviceToHost, st), "copy results");
+        CK(cudaStreamSynchronize(st), "backward sync");
+    }
+    std::vector<double> gwl((size_t)nl * 4 * no), gws((size_t)3 * nl * 4 * no);
+    CK(cudaMemcpyAsync(gwl.data(), ctx->ws + L.GWL, gwl.size() * 8, cudaMemcpyDeviceToHost, st), "copy gradients");
+    CK(cudaMemcpyAsync(gws.data(), ctx->ws + L.GWS, gws.size() * 8, cudaMemcpyDeviceToHost, st), "copy gradients");
+    CK(cudaMemcpyAsync(d_eps_host, ctx->ws + L.d_eps, (size_t)no * 8, cudaMemcpyDeviceToHost, st), "copy gradients");
+    CK(cudaStreamSynchronize(st), "backward sync");
+    // Fold dE/dW back to dE/dC: W^{Lc}_{mu k} = C^{Lc}_{mu k}; W^{Sc'}_{(j,mu) k} =
+    // sum_s sigma_j[c'][s] C^{Ss}_{mu k}, so dE/dC^{Ss} = sum_{j,c'} conj(sigma_j[c'][s]) dE/dW^{Sc'}.
+    const double sig_re[3][2][2] = {{{0, 1}, {1, 0}}, {{0, 0}, {0, 0}}, {{1, 0}, {0, -1}}};
+    const double sig_im[3][2][2] = {{{0, 0}, {0, 0}}, {{0, -1}, {1, 0}}, {{0, 0}, {0, 0}}};
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < nl; ++mu)
+            for (int k = 0; k < no; ++k) {
+                const size_t src = (((size_t)mu * 2 + c) * no + k) * 2, dst = (((size_t)c * nl + mu) * no + k) * 2;
+                d_C_host[dst] = gwl[src];
+                d_C_host[dst + 1] = gwl[src + 1];
+            }
+    for (int s_ = 0; s_ < 2; ++s_)
+        for (int mu = 0; mu < nl; ++mu)
+            for (int k = 0; k < no; ++k) {
+                double re = 0.0, im = 0.0;
+                for (int j = 0; j < 3; ++j)
+                    for (int cp = 0; cp < 2; ++cp) {
+                        const size_t src = ((((size_t)j * nl + mu) * 2 + cp) * no + k) * 2;
+                        const double gr = gws[src], gi = gws[src + 1];
+                        const double sr_ = sig_re[j][cp][s_], si = -sig_im[j][cp][s_];  // conj(sigma)
+                        re += sr_ * gr - si * gi;
+                        im += sr_ * gi + si * gr;
+                    }
+                const size_t dst = (((size_t)(2 + s_) * nl + mu) * no + k) * 2;
+                d_C_host[dst] = re;
+                d_C_host[dst + 1] = im;
+            }
+    if (energy_host) {
+        double e = 0.0, c = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double y = per[i] - c, t = e + y;
+            c = (t - e) - y;
+            e = t;
+        }
+        *energy_host = e / (double)n;
+    }
+    for (int k = 0; k < no; ++k)
+        if (!std::isfinite(d_eps_host[k])) return ctx->fail(MCMP2_ENONFINITE, "non-finite gradient");
     return MCMP2_OK;
 }
 
