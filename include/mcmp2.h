@@ -221,13 +221,15 @@ int mcmp2_restore(mcmp2_ctx *ctx, const void *buf_host, size_t bytes);
  * stream); the call does not wait for it.
  *
  * Scratch: the per-tile partial sums live in a fixed array of
- * MCMP2_NOALLOC_MAX_PARTIALS doubles (512 KiB) inside the library, held on
- * every GPU that loads the library until the process exits.  It needs
+ * MCMP2_NOALLOC_MAX_PARTIALS doubles (512 KiB, plus about 1 KiB for the
+ * reduction's per-block sums) inside the library, held on every GPU that
+ * loads the library until the process exits.  It needs
  * n_tau * ceil(m/8) (ceil(m/8) + 1) / 2 <= MCMP2_NOALLOC_MAX_PARTIALS (for
  * example m = 1024 with n_tau <= 7); larger sizes return MCMP2_ENOSPACE
  * before any work is issued.  The array is shared by all calls and keeps the
  * last call's contents; every entry a call reads is first written by that
- * call, so nothing needs clearing.  Calls that overlap on the GPU (on
+ * call, and the reduction's completion counter is cleared at the start of
+ * each call.  Calls that overlap on the GPU (on
  * different streams, or from different threads) race on the array and give
  * wrong results: serialise them.  The first call on each device looks up the
  * array's device address (with that device current); make that first call

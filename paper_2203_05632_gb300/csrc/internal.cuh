@@ -99,11 +99,11 @@ __device__ __forceinline__ double weight_g(const DevSystem &s, double x, double 
 // context's stream and return cudaGetLastError() of the launch.
 // ---------------------------------------------------------------------------
 cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long long *step,
-                              uint64_t seed, double delta, unsigned long long *accepted,
+                              uint64_t seed, double delta, unsigned long long *accepted, double *a,
                               cudaStream_t st);
 cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, cudaStream_t st);
 cudaError_t launch_times(const DevSystem &s, const unsigned long long *step, uint64_t seed,
-                         const double *tau_given, double *tau, double *scale, cudaStream_t st);
+                         const double *tau_given, double *tau, double *scale, float *scale_f, cudaStream_t st);
 cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t st);
 
 template <typename T>
@@ -119,9 +119,15 @@ cudaError_t launch_adjoint_time(const DevSystem &s, const double *B, const doubl
                                 double *Ys, double *partials, double *GWL, double *GWS, double *d_eps,
                                 cudaStream_t st);
 
+// Reduction scratch: RED_BLOCKS (sum, error) pairs and a completion counter.
+constexpr int RED_BLOCKS = 64;
+struct ReduceScratch {
+    double sum[RED_BLOCKS], err[RED_BLOCKS];
+    unsigned int done;
+};
 cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tiles, double *out_slot,
                           Stats *stats, int update_stats, unsigned long long *step_to_advance,
-                          cudaStream_t st);
+                          ReduceScratch *scratch, cudaStream_t st);
 
 __host__ __device__ inline int pair_blocks(int m, int tile_pairs) { return (m + tile_pairs - 1) / tile_pairs; }
 __host__ __device__ inline int n_tiles_for(int m, int tile_pairs)

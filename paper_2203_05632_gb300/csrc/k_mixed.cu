@@ -109,7 +109,7 @@ struct SpinorMaps {
 };
 
 struct SpinorArgs {
-    const double *scale;  // [n_tau][n_orb]
+    const float *scale;   // [n_tau][n_orb]
     __nv_bfloat16 *occ;   // [n_tau][4][rows][k_occ_pad]
     __nv_bfloat16 *vir;   // [n_tau][4][rows][k_vir_pad]
     int *abort_flag;
@@ -278,12 +278,12 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                         if (col >= kpad) continue;
                         for (int t = 0; t < args.n_tau; ++t) {
                             uint32_t rh[4], rl[4], ih[4], il[4];
+                            const float *srow = args.scale + (size_t)t * args.n_orb;
 #pragma unroll
                             for (int i = 0; i < 8; i += 2) {
                                 const int k0 = k_base + col + i;
-                                const float s0 = k0 < k_end ? (float)args.scale[(size_t)t * args.n_orb + k0] : 0.f;
-                                const float s1 =
-                                    k0 + 1 < k_end ? (float)args.scale[(size_t)t * args.n_orb + k0 + 1] : 0.f;
+                                const float s0 = k0 < k_end ? srow[k0] : 0.f;
+                                const float s1 = k0 + 1 < k_end ? srow[k0 + 1] : 0.f;
                                 const float xr0 = re[8 * g + i] * s0, xr1 = re[8 * g + i + 1] * s1;
                                 const float xi0 = im[8 * g + i] * s0, xi1 = im[8 * g + i + 1] * s1;
                                 const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
@@ -781,7 +781,7 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
 }
 
 int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *r,
-               const double *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
+               const float *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
                cudaEvent_t *ev, int *n_launches, int *n_pair_launches)
 {
     if (!plan.ready) {

@@ -24,26 +24,13 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
     err = (a - (s - bb)) + (b - bb);
 }
 
-constexpr int RED_THREADS = 512;
+constexpr int RED_THREADS = 256;
 
-// One block.  partials: [n_tau][n_tiles].  Each thread forms a compensated sum
-// of a strided slice, then a fixed pairwise tree combines the (sum, error)
-// pairs with error-free additions, so the result is deterministic and carries
-// the compensation of every level.
-__global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, const double *__restrict__ partials,
-                                                             int n_tiles, double *__restrict__ out_slot,
-                                                             Stats *__restrict__ st, int update,
-                                                             unsigned long long *__restrict__ step)
+// Combine (sum, error) pairs held in shared memory by a fixed pairwise tree.
+__device__ void tree_reduce(double *sv, double *se, int n_active)
 {
-    __shared__ double sv[RED_THREADS], se[RED_THREADS];
-    const int total = n_tau * n_tiles;
-    double s = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < total; i += RED_THREADS) kahan_add(s, c, partials[i]);
-    sv[threadIdx.x] = s;
-    se[threadIdx.x] = -c;
-    __syncthreads();
     for (int stride = RED_THREADS / 2; stride > 0; stride >>= 1) {
-        if (threadIdx.x < stride) {
+        if (threadIdx.x < stride && threadIdx.x + stride < n_active) {
             double sum, err;
             two_sum(sv[threadIdx.x], sv[threadIdx.x + stride], sum, err);
             sv[threadIdx.x] = sum;
@@ -51,7 +38,44 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, c
         }
         __syncthreads();
     }
+}
+
+// RED_BLOCKS blocks each reduce a fixed contiguous slice of partials
+// [n_tau][n_tiles] with compensated sums and a pairwise tree of error-free
+// additions; the last block to finish combines the slices in block order and
+// updates the statistics.  The result does not depend on scheduling.
+__global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, const double *__restrict__ partials,
+                                                             int n_tiles, double *__restrict__ out_slot,
+                                                             Stats *__restrict__ st, int update,
+                                                             unsigned long long *__restrict__ step,
+                                                             ReduceScratch *__restrict__ scratch)
+{
+    __shared__ double sv[RED_THREADS], se[RED_THREADS];
+    __shared__ bool last;
+    const int total = n_tau * n_tiles;
+    const int per = (total + RED_BLOCKS - 1) / RED_BLOCKS;
+    const int lo = blockIdx.x * per, hi = min(total, lo + per);
+    double s = 0.0, c = 0.0;
+    for (int i = lo + threadIdx.x; i < hi; i += RED_THREADS) kahan_add(s, c, partials[i]);
+    sv[threadIdx.x] = s;
+    se[threadIdx.x] = -c;
+    __syncthreads();
+    tree_reduce(sv, se, RED_THREADS);
+    if (threadIdx.x == 0) {
+        scratch->sum[blockIdx.x] = sv[0];
+        scratch->err[blockIdx.x] = se[0];
+        __threadfence();
+        last = atomicAdd(&scratch->done, 1u) == RED_BLOCKS - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sv[threadIdx.x] = threadIdx.x < RED_BLOCKS ? ((volatile double *)scratch->sum)[threadIdx.x] : 0.0;
+    se[threadIdx.x] = threadIdx.x < RED_BLOCKS ? ((volatile double *)scratch->err)[threadIdx.x] : 0.0;
+    __syncthreads();
+    tree_reduce(sv, se, RED_BLOCKS);
     if (threadIdx.x != 0) return;
+    scratch->done = 0;
     const double S = sv[0] + se[0];
     const double npairs = 0.5 * (double)m * (double)(m - 1);
     const double value = S / npairs / (double)n_tau;
@@ -78,10 +102,10 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, c
 
 cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tiles, double *out_slot,
                           Stats *stats, int update_stats, unsigned long long *step_to_advance,
-                          cudaStream_t st)
+                          ReduceScratch *scratch, cudaStream_t st)
 {
-    reduce_kernel<<<1, RED_THREADS, 0, st>>>(s.n_tau, s.m, partials, n_tiles, out_slot, stats, update_stats,
-                                     step_to_advance);
+    reduce_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(s.n_tau, s.m, partials, n_tiles, out_slot, stats, update_stats,
+                                                       step_to_advance, scratch);
     return cudaGetLastError();
 }
 

@@ -9,45 +9,66 @@ namespace mcmp2 {
 // displacement in [-delta, delta]^3; the move is accepted with probability
 // min(1, w'/w) with w = g(r1) g(r2) / r12 (the 1/N_g cancels).  FP64 with
 // explicit rounding so the same counters give the same walk on the host.
+// Four lanes share a pair: lane j evaluates g for electron j&1 at the old (j<2)
+// or proposed (j>=2) position (g is FP64-exp bound on GB300).  The pair's
+// weight factor a_p = N_g / (g(r1) g(r2)) at the resulting positions is
+// written as well (a may be null).
 __global__ void metropolis_kernel(DevSystem s, double *__restrict__ r,
                                   const unsigned long long *__restrict__ step_ptr, uint64_t seed,
-                                  double delta, unsigned long long *__restrict__ accepted)
+                                  double delta, unsigned long long *__restrict__ accepted, double *__restrict__ a)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned int acc = 0;
-    if (p < s.m) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = gid >> 2, j = gid & 3;
+    const bool live = p < s.m;
+    const int lane = threadIdx.x & 31, g0 = lane & ~3;
+    double pos[3] = {0.0, 0.0, 0.0};
+    double o1[3] = {0.0, 0.0, 0.0}, o2[3] = {0.0, 0.0, 0.0}, n1[3] = {0.0, 0.0, 0.0}, n2[3] = {0.0, 0.0, 0.0};
+    uint32_t u_acc = 0;
+    if (live) {
         const uint64_t step = *step_ptr;
-        const uint4 a = draw4(seed, step, (uint32_t)p, 0u);
-        const uint4 b = draw4(seed, step, (uint32_t)p, 1u);
-        const uint32_t u[7] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
-        double *r1 = r + 6 * p, *r2 = r1 + 3;
-        double o1[3], o2[3], n1[3], n2[3];
+        const uint4 A = draw4(seed, step, (uint32_t)p, 0u);
+        const uint4 B = draw4(seed, step, (uint32_t)p, 1u);
+        const uint32_t u[7] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z};
+        const double *r1 = r + 6 * p, *r2 = r1 + 3;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            o1[j] = r1[j];
-            o2[j] = r2[j];
-            n1[j] = __dadd_rn(o1[j], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[j])), 1.0)));
-            n2[j] = __dadd_rn(o2[j], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[3 + j])), 1.0)));
+        for (int k = 0; k < 3; ++k) {
+            o1[k] = r1[k];
+            o2[k] = r2[k];
+            n1[k] = __dadd_rn(o1[k], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[k])), 1.0)));
+            n2[k] = __dadd_rn(o2[k], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[3 + k])), 1.0)));
         }
-        auto pair_w = [&](const double *x1, const double *x2) {
-            const double dx = __dsub_rn(x1[0], x2[0]), dy = __dsub_rn(x1[1], x2[1]), dz = __dsub_rn(x1[2], x2[2]);
-            const double r12 = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-            return __ddiv_rn(__dmul_rn(weight_g(s, x1[0], x1[1], x1[2]), weight_g(s, x2[0], x2[1], x2[2])), r12);
-        };
-        const double w_old = pair_w(o1, o2);
-        const double w_new = pair_w(n1, n2);
-        if (__dmul_rn(u32_open(u[6]), w_old) < w_new) {
+        u_acc = u[6];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                r1[j] = n1[j];
-                r2[j] = n2[j];
+        for (int k = 0; k < 3; ++k) pos[k] = (j == 0) ? o1[k] : (j == 1) ? o2[k] : (j == 2) ? n1[k] : n2[k];
+    }
+    const double gj = live ? weight_g(s, pos[0], pos[1], pos[2]) : 1.0;
+    const double g1o = __shfl_sync(0xffffffffu, gj, g0 + 0), g2o = __shfl_sync(0xffffffffu, gj, g0 + 1);
+    const double g1n = __shfl_sync(0xffffffffu, gj, g0 + 2), g2n = __shfl_sync(0xffffffffu, gj, g0 + 3);
+    unsigned int acc = 0;
+    if (live && j == 0) {
+        auto r12 = [](const double *x1, const double *x2) {
+            const double dx = __dsub_rn(x1[0], x2[0]), dy = __dsub_rn(x1[1], x2[1]), dz = __dsub_rn(x1[2], x2[2]);
+            return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        };
+        const double w_old = __ddiv_rn(__dmul_rn(g1o, g2o), r12(o1, o2));
+        const double w_new = __ddiv_rn(__dmul_rn(g1n, g2n), r12(n1, n2));
+        double *r1 = r + 6 * p, *r2 = r1 + 3;
+        double ga = g1o, gb = g2o;
+        if (__dmul_rn(u32_open(u_acc), w_old) < w_new) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                r1[k] = n1[k];
+                r2[k] = n2[k];
             }
+            ga = g1n;
+            gb = g2n;
             acc = 1;
         }
+        if (a) a[p] = s.Ng / (ga * gb);
     }
     // One atomic per warp.
     const unsigned int total = __reduce_add_sync(0xffffffffu, acc);
-    if ((threadIdx.x & 31) == 0 && total) atomicAdd(accepted, (unsigned long long)total);
+    if (lane == 0 && total) atomicAdd(accepted, (unsigned long long)total);
 }
 
 // a_p = N_g / (g(r1p) g(r2p)): with 1/(w w) this is the weight factor of a pair of pairs.
@@ -70,7 +91,7 @@ __global__ void pair_weights_kernel(DevSystem s, const double *__restrict__ r, d
 // is at most 1 and the four shifts of a pair of pairs multiply to exp(lambda tau).
 __global__ void times_kernel(DevSystem s, const unsigned long long *__restrict__ step_ptr, uint64_t seed,
                              const double *__restrict__ tau_given, double *__restrict__ tau,
-                             double *__restrict__ scale)
+                             double *__restrict__ scale, float *__restrict__ scale_f)
 {
     const int t = blockIdx.x;
     __shared__ double tt;
@@ -90,18 +111,21 @@ __global__ void times_kernel(DevSystem s, const unsigned long long *__restrict__
     for (int k = threadIdx.x; k < s.n_orb; k += blockDim.x) {
         const double e = s.eps[k];
         const double arg = (k < s.n_occ) ? (e - s.eps_homo) : -(e - s.eps_lumo);
-        scale[(size_t)t * s.n_orb + k] = exp(0.5 * arg * x);
+        const double v = exp(0.5 * arg * x);
+        scale[(size_t)t * s.n_orb + k] = v;
+        if (scale_f) scale_f[(size_t)t * s.n_orb + k] = (float)v;
     }
 }
 
 __global__ void advance_step_kernel(unsigned long long *step) { *step += 1ull; }
 
 cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long long *step,
-                              uint64_t seed, double delta, unsigned long long *accepted,
+                              uint64_t seed, double delta, unsigned long long *accepted, double *a,
                               cudaStream_t st)
 {
-    const int threads = 32;  // FP64 exp-bound: spread the pairs over as many SMs as possible
-    metropolis_kernel<<<(s.m + threads - 1) / threads, threads, 0, st>>>(s, r, step, seed, delta, accepted);
+    const int threads = 64;  // FP64 exp-bound: spread the 4 m lanes over as many SMs as possible
+    const int lanes = 4 * s.m;
+    metropolis_kernel<<<(lanes + threads - 1) / threads, threads, 0, st>>>(s, r, step, seed, delta, accepted, a);
     return cudaGetLastError();
 }
 
@@ -113,9 +137,9 @@ cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, 
 }
 
 cudaError_t launch_times(const DevSystem &s, const unsigned long long *step, uint64_t seed,
-                         const double *tau_given, double *tau, double *scale, cudaStream_t st)
+                         const double *tau_given, double *tau, double *scale, float *scale_f, cudaStream_t st)
 {
-    times_kernel<<<s.n_tau, 256, 0, st>>>(s, step, seed, tau_given, tau, scale);
+    times_kernel<<<s.n_tau, 256, 0, st>>>(s, step, seed, tau_given, tau, scale, scale_f);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Offsets of every array inside the caller's workspace.
 struct Layout {
     size_t centres, wcoef, shell_centre, shell_alpha, shell_coef, fn_shell, fn_pow, eps, WL, WS;
-    size_t r, a, tau, scale, step, burn_acc, stats, per_step, stage_r, stage_tau;
+    size_t r, a, tau, scale, scale_f, step, burn_acc, stats, per_step, stage_r, stage_tau, red;
     size_t B, phi, partials;
     size_t Ybar, Ys, GWL, GWS, d_eps;  // adjoint buffers (FP64 form)
     MixedLayout mixed;
@@ -62,6 +62,8 @@ Layout make_layout(const mcmp2_dims &d, int precision)
     L.a = take(m * 8);
     L.tau = take(d.n_tau * 8);
     L.scale = take(d.n_tau * no * 8);
+    L.scale_f = take(d.n_tau * no * 4);
+    L.red = take(sizeof(ReduceScratch));
     L.step = take(8);
     L.burn_acc = take(8);
     L.stats = take(sizeof(Stats));
@@ -219,6 +221,8 @@ int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, siz
     ctx->L = L;
     ctx->ws = static_cast<char *>(dptr);
     ctx->ws_bytes = bytes;
+    CK(cudaMemsetAsync(ctx->ws + L.red, 0, sizeof(ReduceScratch), ctx->stream), "clear reduction scratch");
+    CK(cudaStreamSynchronize(ctx->stream), "bind sync");
     ctx->bound = true;
     ctx->loaded = ctx->walkers = false;
     return MCMP2_OK;
@@ -405,7 +409,7 @@ int reset_stats(mcmp2_ctx *ctx)
 // The integrand engine for one step: from positions r and times (drawn or
 // given) to I'_n in out_slot.  Optionally updates statistics and advances the step.
 int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uint64_t seed, double *out_slot,
-                   int update, bool advance)
+                   int update, bool advance, bool weights_ready = false)
 {
     const Layout &L = ctx->L;
     const DevSystem &S = ctx->sys;
@@ -415,9 +419,13 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
     double *tau = ctx->at<double>(L.tau);
     double *scale = ctx->at<double>(L.scale);
     double *partials = ctx->at<double>(L.partials);
-    CK(launch_pair_weights(S, r, a, st), "pair weights");
-    CK(launch_times(S, step, seed, tau_given, tau, scale, st), "imaginary times");
-    ctx->launches += 2;
+    if (!weights_ready) {
+        CK(launch_pair_weights(S, r, a, st), "pair weights");
+        ctx->launches += 1;
+    }
+    float *scale_f = ctx->precision == MCMP2_MIXED ? ctx->at<float>(L.scale_f) : nullptr;
+    CK(launch_times(S, step, seed, tau_given, tau, scale, scale_f, st), "imaginary times");
+    ctx->launches += 1;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (ctx->timing) {
         CK(cudaEventCreate(&ev[0]), "event");
@@ -437,14 +445,14 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         ctx->pair_launches += 1;
     } else {
         int n_launch = 0, n_pair = 0;
-        const int rc = mixed_step(ctx->mixed, S, L.mixed, ctx->ws, r, scale, a, partials, st, ctx->err,
+        const int rc = mixed_step(ctx->mixed, S, L.mixed, ctx->ws, r, scale_f, a, partials, st, ctx->err,
                                   ctx->timing ? ev : nullptr, &n_launch, &n_pair);
         if (rc != MCMP2_OK) return rc;
         ctx->launches += n_launch;
         ctx->pair_launches += n_pair;
     }
     CK(launch_reduce(S, partials, L.n_tiles, out_slot, ctx->at<Stats>(L.stats), update, advance ? step : nullptr,
-                     st),
+                     ctx->at<ReduceScratch>(L.red), st),
        "step reduction");
     ctx->launches += 1;
     return MCMP2_OK;
@@ -483,7 +491,8 @@ int mcmp2_set_walkers(mcmp2_ctx *ctx, const double *r_host, uint64_t seed, int64
         const int64_t len = std::min<int64_t>(MCMP2_ADAPT_WINDOW, burn_in - done);
         CK(cudaMemsetAsync(acc, 0, 8, st), "reset acceptance");
         for (int64_t i = 0; i < len; ++i) {
-            CK(launch_metropolis(ctx->sys, ctx->at<double>(L.r), step, seed, ctx->delta, acc, st), "metropolis");
+            CK(launch_metropolis(ctx->sys, ctx->at<double>(L.r), step, seed, ctx->delta, acc, nullptr, st),
+               "metropolis");
             CK(launch_advance_step(step, st), "advance step");
         }
         if (len == MCMP2_ADAPT_WINDOW) {
@@ -514,10 +523,11 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
     Stats *stats = ctx->at<Stats>(L.stats);
     double *r = ctx->at<double>(L.r);
     for (int64_t i = 0; i < n; ++i) {
-        CK(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta, &stats->accepted, st),
+        CK(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta, &stats->accepted,
+                             ctx->at<double>(L.a), st),
            "metropolis");
         ctx->launches += 1;
-        const int rc = step_integrand(ctx, r, nullptr, seed, ctx->at<double>(L.per_step), 1, true);
+        const int rc = step_integrand(ctx, r, nullptr, seed, ctx->at<double>(L.per_step), 1, true, true);
         if (rc) return rc;
     }
     if (out) {
@@ -616,7 +626,7 @@ int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double
         for (int j = 0; j < len; ++j) {
             const double *rj = sr + (size_t)j * m * 6;
             CK(launch_pair_weights(S, rj, a, st), "pair weights");
-            CK(launch_times(S, step, 0, stau + (size_t)j * nt, tau, scale, st), "imaginary times");
+            CK(launch_times(S, step, 0, stau + (size_t)j * nt, tau, scale, nullptr, st), "imaginary times");
             CK(launch_basis<double>(S, rj, B, st), "basis values");
             CK(launch_spinors_f64(S, B, phi, st), "spinor formation");
             for (int t = 0; t < nt; ++t) {
@@ -626,7 +636,9 @@ int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double
                                        ctx->at<double>(L.d_eps), st),
                    "adjoint");
             }
-            CK(launch_reduce(S, partials, L.n_tiles, slots + j, ctx->at<Stats>(L.stats), 0, nullptr, st), "reduce");
+            CK(launch_reduce(S, partials, L.n_tiles, slots + j, ctx->at<Stats>(L.stats), 0, nullptr,
+                             ctx->at<ReduceScratch>(L.red), st),
+               "reduce");
         }
         CK(cudaMemcpyAsync(per.data() + s0, slots, sizeof(double) * len, cudaMemcpyDeviceToHost, st), "copy results");
         CK(cudaStreamSynchronize(st), "backward sync");

@@ -39,7 +39,7 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
 // contraction writing partials [n_tau][n_tiles].  ev (if non-null) gets
 // ev[0], ev[1] recorded around the contraction launch.
 int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *r,
-               const double *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
+               const float *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
                cudaEvent_t *ev, int *n_launches, int *n_pair_launches);
 
 // Reads (synchronously) and clears the device flag a timed-out kernel sets.

@@ -13,8 +13,11 @@ namespace {
 
 // Scratch for the per-tile partial sums of one call: [n_tau][n_tiles] doubles.
 // Every GPU that loads the library holds this array until the process exits.
+// The reduction's per-block (sum, error) pairs and completion counter follow
+// the partial sums in the same array.
 constexpr size_t NOALLOC_MAX_PARTIALS = MCMP2_NOALLOC_MAX_PARTIALS;
-static __device__ __align__(256) double g_pair_partials[NOALLOC_MAX_PARTIALS];
+constexpr size_t REDUCE_DOUBLES = (sizeof(mcmp2::ReduceScratch) + sizeof(double) - 1) / sizeof(double);
+static __device__ __align__(256) double g_pair_partials[NOALLOC_MAX_PARTIALS + REDUCE_DOUBLES];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mutex;
@@ -59,9 +62,12 @@ extern "C" int mcmp2_pair_sum_f64_noalloc(int m, int n_occ, int n_vir, int n_tau
     s.lambda = lambda;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // Every partial is written by its tile before the reduction reads it, so
-    // nothing left in the array by an earlier call needs clearing.
+    // the partials need no clearing; the reduction's completion counter must
+    // start at zero and is cleared here (a plain memset, no allocation).
+    auto *red = reinterpret_cast<mcmp2::ReduceScratch *>(partials + NOALLOC_MAX_PARTIALS);
+    if (cudaMemsetAsync(&red->done, 0, sizeof(red->done), st) != cudaSuccess) return MCMP2_ECUDA;
     if (mcmp2::launch_pairs_f64(s, phi, scale, a, partials, st) != cudaSuccess) return MCMP2_ECUDA;
-    if (mcmp2::launch_reduce(s, partials, n_tiles, out, nullptr, 0, nullptr, st) != cudaSuccess)
+    if (mcmp2::launch_reduce(s, partials, n_tiles, out, nullptr, 0, nullptr, red, st) != cudaSuccess)
         return MCMP2_ECUDA;
     return MCMP2_OK;
 }
