@@ -110,6 +110,7 @@ template <typename T>
 cudaError_t launch_basis(const DevSystem &s, const double *r, T *B, cudaStream_t st);
 
 cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi, cudaStream_t st);
+cudaError_t prepare_f64();  // sets the FP64 contraction kernel's shared-memory limit
 cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale,
                              const double *a, double *partials, cudaStream_t st);
 

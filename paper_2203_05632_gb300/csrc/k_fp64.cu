@@ -295,15 +295,23 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
     }
 }
 
+static bool g_f64_configured = false;
+
+cudaError_t prepare_f64()
+{
+    const cudaError_t e =
+        cudaFuncSetAttribute(pairs_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F64Smem));
+    if (e == cudaSuccess) g_f64_configured = true;
+    return e;
+}
+
 cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale, const double *a,
                              double *partials, cudaStream_t st)
 {
-    static bool configured = false;
     const size_t smem = sizeof(F64Smem);
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(pairs_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!g_f64_configured) {
+        const cudaError_t e = prepare_f64();
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     const int n_tiles = n_tiles_for(s.m, F64_TP);
     dim3 grid(n_tiles, s.n_tau);

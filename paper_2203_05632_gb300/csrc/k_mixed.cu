@@ -101,8 +101,13 @@ constexpr int SP_STAGES = 4;
 constexpr int SP_STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo
 constexpr int SP_THREADS = 192;                 // TMA warp, MMA warp, 4 epilogue warps
 constexpr int SP_TMEM_COLS = 256;               // two 128-column accumulators
+constexpr int SP_MAX_TAU = 64;                  // scale staging capacity (the API limits n_tau to 64)
+constexpr int SP_ROW_BYTES = 144;               // staged row: 64 BF16 (128 B) + 16 B pad against bank conflicts
+constexpr int SP_WARP_STAGE = 4 * 32 * SP_ROW_BYTES;  // 4 planes x 32 rows per epilogue warp
 constexpr int SP_BARS_OFF = SP_STAGES * SP_STAGE_BYTES;
-constexpr int SP_SMEM = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16 + 1024;
+constexpr int SP_SCALE_OFF = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16;
+constexpr int SP_WSTAGE_OFF = SP_SCALE_OFF + SP_MAX_TAU * 64 * 4;
+constexpr int SP_SMEM = SP_WSTAGE_OFF + 4 * SP_WARP_STAGE + 1024;
 
 struct SpinorMaps {
     CUtensorMap m[8];  // 0..3: A_L hi, A_L lo, B_L hi, B_L lo; 4..7: the same for the gradient part
@@ -245,62 +250,88 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             mbar_drain(&empty[stage], phase, TIMEOUT_NS);
         }
     } else {
+        // Epilogue: each lane owns one position row of the tile.  For every time
+        // the warp stages its 32 rows x 64 orbitals of the 4 planes in shared
+        // memory, then writes them as whole 128-byte row segments (8 lanes per
+        // row), so each store instruction touches 4 lines instead of 32.
+        const int ew = warp - 2;
         const int quarter = warp & 3;
-        const int row = 32 * quarter + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+        float *sscale = reinterpret_cast<float *>(smem + SP_SCALE_OFF);  // [n_tau][64]
+        unsigned char *wstage = smem + SP_WSTAGE_OFF + ew * SP_WARP_STAGE;
         int buf = 0;
         uint32_t ephase[2] = {0, 0};
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
             int mt, c4, kb;
             sp_tile(tile, args.n_kb, mt, c4, kb);
             const bool got = mbar_wait(&tfull[buf], ephase[buf], args.abort_flag, 14, TIMEOUT_NS);
-            if (bar_any<1, 128>(!got)) break;
+            if (bar_any<1, 128>(!got)) break;  // also: every epilogue warp is done with the previous scales
             ephase[buf] ^= 1u;
             fence_after();
-            const int x = mt * 128 + row;
             const bool occ = kb < args.n_kb_occ;
             const int kl = occ ? kb : kb - args.n_kb_occ;
             const int kpad = occ ? args.k_occ_pad : args.k_vir_pad;
-            const int k_base = occ ? 0 : args.n_occ;              // absolute index of the region's first orbital
-            const int k_end = occ ? args.n_occ : args.n_orb;      // one past the region's last orbital
+            const int k_first = (occ ? 0 : args.n_occ) + kl * 64;  // absolute index of the block's first orbital
+            const int k_end = occ ? args.n_occ : args.n_orb;       // one past the region's last orbital
             __nv_bfloat16 *planes = occ ? args.occ : args.vir;
             const size_t plane_elems = (size_t)args.rows * kpad;
-            const size_t row_off = (size_t)(4 * x + c4) * kpad;
-            for (int j = 0; j < 4; ++j) {
-                float re[16], im[16];
-                tmem_ld<16>(lane_addr + 128u * buf + 16u * j, re);
-                tmem_ld<16>(lane_addr + 128u * buf + 64u + 16u * j, im);
-                tmem_wait_ld();
-                if (x < args.P) {
+            for (int i = threadIdx.x - 64; i < 64 * args.n_tau; i += 128) {
+                const int t = i >> 6, k = k_first + (i & 63);
+                sscale[i] = k < k_end ? args.scale[(size_t)t * args.n_orb + k] : 0.f;
+            }
+            bar_sync<1, 128>();
+            for (int t = 0; t < args.n_tau; ++t) {
+                const float *st_ = sscale + 64 * t;
+#pragma unroll 1
+                for (int j = 0; j < 4; ++j) {
+                    float re[16], im[16];
+                    tmem_ld<16>(lane_addr + 128u * buf + 16u * j, re);
+                    tmem_ld<16>(lane_addr + 128u * buf + 64u + 16u * j, im);
+                    tmem_wait_ld();
+                    uint32_t rh[8], rl[8], ih[8], il[8];
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
-                        const int col = kl * 64 + 16 * j + 8 * g;
-                        if (col >= kpad) continue;
-                        for (int t = 0; t < args.n_tau; ++t) {
-                            uint32_t rh[4], rl[4], ih[4], il[4];
-                            const float *srow = args.scale + (size_t)t * args.n_orb;
+                    for (int i = 0; i < 16; i += 2) {
+                        const float s0 = st_[16 * j + i], s1 = st_[16 * j + i + 1];
+                        const float xr0 = re[i] * s0, xr1 = re[i + 1] * s1;
+                        const float xi0 = im[i] * s0, xi1 = im[i + 1] * s1;
+                        const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
+                        const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
+                        rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
+                        ih[i / 2] = *reinterpret_cast<const uint32_t *>(&hi);
+                        rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
+                        il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
+                    }
+                    unsigned char *myrow = wstage + lane * SP_ROW_BYTES + 32 * j;
+                    uint4 *d0 = reinterpret_cast<uint4 *>(myrow), *d1 = reinterpret_cast<uint4 *>(myrow + 32 * SP_ROW_BYTES);
+                    uint4 *d2 = reinterpret_cast<uint4 *>(myrow + 64 * SP_ROW_BYTES);
+                    uint4 *d3 = reinterpret_cast<uint4 *>(myrow + 96 * SP_ROW_BYTES);
+                    d0[0] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                    d0[1] = make_uint4(rh[4], rh[5], rh[6], rh[7]);
+                    d1[0] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                    d1[1] = make_uint4(rl[4], rl[5], rl[6], rl[7]);
+                    d2[0] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                    d2[1] = make_uint4(ih[4], ih[5], ih[6], ih[7]);
+                    d3[0] = make_uint4(il[0], il[1], il[2], il[3]);
+                    d3[1] = make_uint4(il[4], il[5], il[6], il[7]);
+                }
+                __syncwarp();
+                const int chunk = lane & 7;
 #pragma unroll
-                            for (int i = 0; i < 8; i += 2) {
-                                const int k0 = k_base + col + i;
-                                const float s0 = k0 < k_end ? srow[k0] : 0.f;
-                                const float s1 = k0 + 1 < k_end ? srow[k0 + 1] : 0.f;
-                                const float xr0 = re[8 * g + i] * s0, xr1 = re[8 * g + i + 1] * s1;
-                                const float xi0 = im[8 * g + i] * s0, xi1 = im[8 * g + i + 1] * s1;
-                                const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
-                                const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
-                                rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
-                                ih[i / 2] = *reinterpret_cast<const uint32_t *>(&hi);
-                                rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
-                                il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
-                            }
-                            __nv_bfloat16 *dst = planes + (size_t)t * 4 * plane_elems + row_off + col;
-                            *reinterpret_cast<uint4 *>(dst) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                            *reinterpret_cast<uint4 *>(dst + plane_elems) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                            *reinterpret_cast<uint4 *>(dst + 2 * plane_elems) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                            *reinterpret_cast<uint4 *>(dst + 3 * plane_elems) = make_uint4(il[0], il[1], il[2], il[3]);
+                for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int r_in = 4 * it + (lane >> 3);
+                        const int x = mt * 128 + 32 * quarter + r_in;
+                        if (x < args.P) {
+                            const uint4 v =
+                                *reinterpret_cast<const uint4 *>(wstage + pl * 32 * SP_ROW_BYTES + r_in * SP_ROW_BYTES +
+                                                                 16 * chunk);
+                            __nv_bfloat16 *dst = planes + ((size_t)t * 4 + pl) * plane_elems + (size_t)(4 * x + c4) * kpad +
+                                                 kl * 64 + 8 * chunk;
+                            *reinterpret_cast<uint4 *>(dst) = v;
                         }
                     }
-                }
+                __syncwarp();
             }
             fence_before();
             __syncwarp();
@@ -508,6 +539,9 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             ephase ^= 1u;
             fence_after();
             const int p = bp * 16 + p_local;
+            // a_q of the tile's 16 q-pairs, one per lane (lane & 15), fetched by shuffle below.
+            const int q_lane = bq * 16 + (lane & 15);
+            const double a_lane = q_lane < args.m ? args.a[q_lane] : 0.0;
             double acc = 0.0;  // sum over this warp's q of Re f_pq a_q
             for (int qb = 0; qb < 4; ++qb) {
                 const int q0 = 8 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
@@ -576,8 +610,9 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                     xr += __shfl_xor_sync(0xffffffffu, xr, 4);
                     const int ql = q0 + qq;
                     const int q = bq * 16 + ql;
+                    const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
                     const bool valid = p < args.m && q < args.m && (bp < bq || p_local < ql);
-                    if (valid) acc += (double)(-0.5f * (direct_re - xr)) * args.a[q];
+                    if (valid) acc += (double)(-0.5f * (direct_re - xr)) * a_q;
                 }
             }
             fence_before();
@@ -673,8 +708,8 @@ MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t
     L.wt_rows = 2 * L.n_kb * 128;
     L.P = 2 * m;
     L.rows = 8 * m;
-    L.k_occ_pad = round8(n_occ);
-    L.k_vir_pad = round8(n_vir);
+    L.k_occ_pad = (n_occ + 63) / 64 * 64;  // whole 64-orbital blocks: each staged row segment is one 128 B line
+    L.k_vir_pad = (n_vir + 63) / 64 * 64;
     L.n_tau = n_tau;
     size_t off = align256(offset);
     auto take = [&](size_t bytes) {

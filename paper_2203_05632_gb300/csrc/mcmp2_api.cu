@@ -137,6 +137,35 @@ struct mcmp2_ctx {
     long long launches = 0, pair_launches = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pair_events;
+    double graph_pair_ms = 0.0;
+    // CUDA graph of one production step (replayed by run_steps)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    uint64_t graph_seed = 0;
+    double graph_delta = 0.0;
+    bool graph_timing = false;
+    long long graph_launches = 0, graph_pair_launches = 0;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    bool gev_pending = false;  // the last replay's contraction events are not yet accumulated
+
+    // Adds the contraction time of the last replay (waits for it to finish).
+    cudaError_t collect_graph_time()
+    {
+        if (!gev_pending) return cudaSuccess;
+        gev_pending = false;
+        cudaError_t e = cudaEventSynchronize(gev[1]);
+        if (e != cudaSuccess) return e;
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, gev[0], gev[1]);
+        if (e == cudaSuccess) graph_pair_ms += t;
+        return e;
+    }
+
+    void drop_graph()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
 
     int fail(int code, const char *fmt, ...)
     {
@@ -195,6 +224,10 @@ void mcmp2_destroy(mcmp2_ctx *ctx)
 {
     if (!ctx) return;
     drop_events(ctx);
+    ctx->drop_graph();
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (auto &e : ctx->gev)
+        if (e) cudaEventDestroy(e);
     mixed_release(ctx->mixed);
     delete ctx;
 }
@@ -225,6 +258,7 @@ int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, siz
     CK(cudaStreamSynchronize(ctx->stream), "bind sync");
     ctx->bound = true;
     ctx->loaded = ctx->walkers = false;
+    ctx->drop_graph();
     return MCMP2_OK;
 }
 
@@ -385,6 +419,8 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     h = fnv1a(h, eps, sizeof(double) * no);
     ctx->digest = h;
     ctx->loaded = true;
+    ctx->drop_graph();  // kernel arguments captured by value (energies, lambda) change with the system
+    if (ctx->precision == MCMP2_FP64) CK(prepare_f64(), "configure FP64 kernels");
     ctx->walkers = false;
     if (ctx->precision == MCMP2_MIXED) {
         const int rc = mixed_prepare(ctx->mixed, S, L.mixed, ctx->ws, WL.data(), WS.data(), st, ctx->err);
@@ -409,11 +445,12 @@ int reset_stats(mcmp2_ctx *ctx)
 // The integrand engine for one step: from positions r and times (drawn or
 // given) to I'_n in out_slot.  Optionally updates statistics and advances the step.
 int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uint64_t seed, double *out_slot,
-                   int update, bool advance, bool weights_ready = false)
+                   int update, bool advance, bool weights_ready = false, cudaStream_t st_in = nullptr,
+                   cudaEvent_t *fixed_ev = nullptr)
 {
     const Layout &L = ctx->L;
     const DevSystem &S = ctx->sys;
-    cudaStream_t st = ctx->stream;
+    cudaStream_t st = st_in ? st_in : ctx->stream;
     unsigned long long *step = ctx->at<unsigned long long>(L.step);
     double *a = ctx->at<double>(L.a);
     double *tau = ctx->at<double>(L.tau);
@@ -427,7 +464,10 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
     CK(launch_times(S, step, seed, tau_given, tau, scale, scale_f, st), "imaginary times");
     ctx->launches += 1;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (ctx->timing) {
+    if (fixed_ev) {
+        ev[0] = fixed_ev[0];
+        ev[1] = fixed_ev[1];
+    } else if (ctx->timing) {
         CK(cudaEventCreate(&ev[0]), "event");
         CK(cudaEventCreate(&ev[1]), "event");
         ctx->pair_events.emplace_back(ev[0], ev[1]);
@@ -446,7 +486,7 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
     } else {
         int n_launch = 0, n_pair = 0;
         const int rc = mixed_step(ctx->mixed, S, L.mixed, ctx->ws, r, scale_f, a, partials, st, ctx->err,
-                                  ctx->timing ? ev : nullptr, &n_launch, &n_pair);
+                                  ev[0] ? ev : nullptr, &n_launch, &n_pair);
         if (rc != MCMP2_OK) return rc;
         ctx->launches += n_launch;
         ctx->pair_launches += n_pair;
@@ -522,13 +562,50 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     Stats *stats = ctx->at<Stats>(L.stats);
     double *r = ctx->at<double>(L.r);
-    for (int64_t i = 0; i < n; ++i) {
-        CK(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta, &stats->accepted,
-                             ctx->at<double>(L.a), st),
-           "metropolis");
+    // One step is captured once into a CUDA graph (its kernels read the step
+    // counter from device memory, so the graph is the same for every step)
+    // and replayed n times on the caller's stream.
+    if (n > 0 && (!ctx->graph || ctx->graph_seed != seed || ctx->graph_delta != ctx->delta ||
+                  ctx->graph_timing != ctx->timing)) {
+        ctx->drop_graph();
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
+        if (ctx->timing && !ctx->gev[0]) {
+            CK(cudaEventCreate(&ctx->gev[0]), "event");
+            CK(cudaEventCreate(&ctx->gev[1]), "event");
+        }
+        const long long l0 = ctx->launches, p0 = ctx->pair_launches;
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int rc = ctx->cuda(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta,
+                                             &stats->accepted, ctx->at<double>(L.a), ctx->cap_stream),
+                           "metropolis");
         ctx->launches += 1;
-        const int rc = step_integrand(ctx, r, nullptr, seed, ctx->at<double>(L.per_step), 1, true, true);
-        if (rc) return rc;
+        if (rc == MCMP2_OK)
+            rc = step_integrand(ctx, r, nullptr, seed, ctx->at<double>(L.per_step), 1, true, true, ctx->cap_stream,
+                                ctx->timing ? ctx->gev : nullptr);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+        ctx->graph_launches = ctx->launches - l0;
+        ctx->graph_pair_launches = ctx->pair_launches - p0;
+        ctx->launches = l0;
+        ctx->pair_launches = p0;
+        if (rc != MCMP2_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        CK(ec, "end capture");
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(ei, "instantiate step graph");
+        ctx->graph_seed = seed;
+        ctx->graph_delta = ctx->delta;
+        ctx->graph_timing = ctx->timing;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (ctx->timing) CK(ctx->collect_graph_time(), "event time");  // before the events are re-recorded
+        CK(cudaGraphLaunch(ctx->graph, st), "launch step graph");
+        ctx->launches += ctx->graph_launches;
+        ctx->pair_launches += ctx->graph_pair_launches;
+        if (ctx->timing) ctx->gev_pending = true;
     }
     if (out) {
         Stats h;
@@ -726,10 +803,13 @@ int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out)
     if (mode == 1 || mode == 2) {
         drop_events(ctx);
         ctx->launches = ctx->pair_launches = 0;
+        CK(ctx->collect_graph_time(), "event time");
+        ctx->graph_pair_ms = 0.0;
         ctx->timing = (mode == 1);
         return MCMP2_OK;
     }
     if (mode != 0 || !out) return ctx->fail(MCMP2_EINVAL, "bad profile mode");
+    CK(ctx->collect_graph_time(), "event time");
     out->launches = ctx->launches;
     out->pair_launches = ctx->pair_launches;
     double ms = 0.0;
@@ -741,7 +821,7 @@ int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out)
             ms += t;
         }
     }
-    out->pair_ms = ms;
+    out->pair_ms = ms + ctx->graph_pair_ms;
     return MCMP2_OK;
 }
 
