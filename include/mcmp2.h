@@ -132,7 +132,9 @@ int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, siz
 int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n_vir,
                       const double *C_host, const double *eps_host);
 
-/* Set the m walker pairs from r_host ([m][2][3]) and run `burn_in` Metropolis
+/* Set the m walker pairs from r_host ([m][2][3]), or, if r_host is NULL, draw
+ * them from g(r1) g(r2) (each electron from the Gaussian mixture g; Philox
+ * counters of the reserved step 2^64 - 1), and run `burn_in` Metropolis
  * steps with seed `seed` (steps numbered from 0), adapting the displacement
  * every MCMP2_ADAPT_WINDOW steps by delta <- delta * clamp(a/0.5, 0.5, 2) with
  * a the window's acceptance fraction.  Resets the statistics and the step

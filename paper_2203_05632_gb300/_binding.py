@@ -181,6 +181,10 @@ class Context:
 
     # -- API -------------------------------------------------------------
     def set_walkers(self, r, seed: int, burn_in: int):
+        """Initial positions [m][2][3], or None to draw them from g(r1) g(r2) on the device."""
+        if r is None:
+            self._check(self.lib.mcmp2_set_walkers(self.h, None, int(seed), int(burn_in)))
+            return
         r = _c(r, np.float64).reshape(self.m, 2, 3)
         self._check(self.lib.mcmp2_set_walkers(self.h, _ptr(r), int(seed), int(burn_in)))
 

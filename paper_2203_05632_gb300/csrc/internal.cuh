@@ -105,6 +105,7 @@ cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, 
 cudaError_t launch_times(const DevSystem &s, const unsigned long long *step, uint64_t seed,
                          const double *tau_given, double *tau, double *scale, float *scale_f, cudaStream_t st);
 cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t st);
+cudaError_t launch_initial_walkers(const DevSystem &s, double *r, uint64_t seed, const double *cdf, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_basis(const DevSystem &s, const double *r, T *B, cudaStream_t st);

@@ -848,9 +848,9 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     const int n_tiles = nb * (nb + 1) / 2;
     PairArgs pa{a, partials, flag, s.m, n_tiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda};
     const int items = n_tiles * s.n_tau;
-    if (ev) cudaEventRecord(ev[0], st);
+    if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
     pairs_mixed_kernel<<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
-    if (ev) cudaEventRecord(ev[1], st);
+    if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("mixed-form launch: ") + cudaGetErrorString(e);

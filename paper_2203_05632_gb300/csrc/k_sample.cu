@@ -119,6 +119,47 @@ __global__ void times_kernel(DevSystem s, const unsigned long long *__restrict__
 
 __global__ void advance_step_kernel(unsigned long long *step) { *step += 1ull; }
 
+// Initial positions drawn from g(r1) g(r2): each electron independently from the
+// Gaussian mixture g (component k of centre I with probability proportional to
+// its mass c_k N(zeta_k) (pi/zeta_k)^{3/2}, given as a cumulative table cdf
+// [2 n_centres]), normal deviates of variance 1/(2 zeta) by Box-Muller.
+// Counters: {lo, hi} of the reserved step 2^64 - 1, index = pair, tags 3 and 4.
+__global__ void initial_walkers_kernel(DevSystem s, double *__restrict__ r, uint64_t seed,
+                                       const double *__restrict__ cdf)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.m) return;
+    const uint64_t step = ~0ull;
+    for (int e = 0; e < 2; ++e) {
+        const uint4 a = draw4(seed, step, (uint32_t)p, 3u + 2u * e);
+        const uint4 b = draw4(seed, step, (uint32_t)p, 4u + 2u * e);
+        const double uc = u32_open(a.x);
+        int comp = 2 * s.n_centres - 1;
+        for (int i = 0; i < 2 * s.n_centres; ++i)
+            if (uc < cdf[i]) {
+                comp = i;
+                break;
+            }
+        const int ic = comp >> 1;
+        const double zeta = s.wcoef[4 * ic + 1 + 2 * (comp & 1)];
+        const double sigma = sqrt(0.5 / zeta);
+        const double u1 = u32_open(a.y), u2 = u32_open(a.z), u3 = u32_open(b.x), u4 = u32_open(b.y);
+        const double rad1 = sqrt(-2.0 * log(u1)), rad2 = sqrt(-2.0 * log(u3));
+        const double z0 = rad1 * cos(6.283185307179586 * u2), z1 = rad1 * sin(6.283185307179586 * u2);
+        const double z2 = rad2 * cos(6.283185307179586 * u4);
+        double *x = r + 6 * p + 3 * e;
+        x[0] = s.centres[3 * ic + 0] + sigma * z0;
+        x[1] = s.centres[3 * ic + 1] + sigma * z1;
+        x[2] = s.centres[3 * ic + 2] + sigma * z2;
+    }
+}
+
+cudaError_t launch_initial_walkers(const DevSystem &s, double *r, uint64_t seed, const double *cdf, cudaStream_t st)
+{
+    initial_walkers_kernel<<<(s.m + 127) / 128, 128, 0, st>>>(s, r, seed, cdf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long long *step,
                               uint64_t seed, double delta, unsigned long long *accepted, double *a,
                               cudaStream_t st)

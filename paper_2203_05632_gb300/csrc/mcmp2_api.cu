@@ -23,7 +23,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Offsets of every array inside the caller's workspace.
 struct Layout {
     size_t centres, wcoef, shell_centre, shell_alpha, shell_coef, fn_shell, fn_pow, eps, WL, WS;
-    size_t r, a, tau, scale, scale_f, step, burn_acc, stats, per_step, stage_r, stage_tau, red;
+    size_t r, a, tau, scale, scale_f, step, burn_acc, stats, per_step, stage_r, stage_tau, red, cdf;
     size_t B, phi, partials;
     size_t Ybar, Ys, GWL, GWS, d_eps;  // adjoint buffers (FP64 form)
     MixedLayout mixed;
@@ -64,6 +64,7 @@ Layout make_layout(const mcmp2_dims &d, int precision)
     L.scale = take(d.n_tau * no * 8);
     L.scale_f = take(d.n_tau * no * 4);
     L.red = take(sizeof(ReduceScratch));
+    L.cdf = take(2 * nc * 8);
     L.step = take(8);
     L.burn_acc = take(8);
     L.stats = take(sizeof(Stats));
@@ -417,6 +418,21 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     h = fnv1a(h, b->shell_coef, sizeof(double) * b->n_shells);
     h = fnv1a(h, C, sizeof(double) * 2 * 4 * (size_t)nl * no);
     h = fnv1a(h, eps, sizeof(double) * no);
+    // Cumulative masses of the weight function's Gaussians, for drawing initial positions.
+    {
+        std::vector<double> cdf(2 * (size_t)b->n_centres);
+        double tot = 0.0;
+        for (int i = 0; i < b->n_centres; ++i)
+            for (int k = 0; k < 2; ++k) {
+                const double c = wcoef[4 * i + 2 * k], z = wcoef[4 * i + 2 * k + 1];
+                tot += std::fabs(c) * std::pow(M_PI / z, 1.5);
+                cdf[2 * i + k] = tot;
+            }
+        for (auto &v : cdf) v /= tot;
+        cdf.back() = 1.0;
+        CK(cudaMemcpyAsync(ctx->ws + L.cdf, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, st), "copy mixture");
+        CK(cudaStreamSynchronize(st), "load sync");
+    }
     ctx->digest = h;
     ctx->loaded = true;
     ctx->drop_graph();  // kernel arguments captured by value (energies, lambda) change with the system
@@ -478,9 +494,9 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         double *phi = ctx->at<double>(L.phi);
         CK(launch_basis<double>(S, r, B, st), "basis values");
         CK(launch_spinors_f64(S, B, phi, st), "spinor formation");
-        if (e0) CK(cudaEventRecord(e0, st), "event");
+        if (e0) CK(cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal), "event");
         CK(launch_pairs_f64(S, phi, scale, a, partials, st), "pair-of-pairs tiles");
-        if (e1) CK(cudaEventRecord(e1, st), "event");
+        if (e1) CK(cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal), "event");
         ctx->launches += 4;
         ctx->pair_launches += 1;
     } else {
@@ -513,13 +529,16 @@ int mcmp2_set_walkers(mcmp2_ctx *ctx, const double *r_host, uint64_t seed, int64
 {
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
-    if (!r_host || burn_in < 0) return ctx->fail(MCMP2_EINVAL, "need initial positions and burn_in >= 0");
+    if (burn_in < 0) return ctx->fail(MCMP2_EINVAL, "burn_in < 0");
     const size_t n = (size_t)ctx->dims.m * 6;
-    if (!all_finite(r_host, n)) return ctx->fail(MCMP2_ENONFINITE, "non-finite walker position");
+    if (r_host && !all_finite(r_host, n)) return ctx->fail(MCMP2_ENONFINITE, "non-finite walker position");
     const Layout &L = ctx->L;
     cudaStream_t st = ctx->stream;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    CK(cudaMemcpyAsync(ctx->ws + L.r, r_host, n * sizeof(double), cudaMemcpyHostToDevice, st), "copy walkers");
+    if (r_host)
+        CK(cudaMemcpyAsync(ctx->ws + L.r, r_host, n * sizeof(double), cudaMemcpyHostToDevice, st), "copy walkers");
+    else
+        CK(launch_initial_walkers(ctx->sys, ctx->at<double>(L.r), seed, ctx->at<double>(L.cdf), st), "initial draw");
     CK(cudaMemsetAsync(ctx->ws + L.step, 0, 8, st), "reset step");
     int rc = reset_stats(ctx);
     if (rc) return rc;

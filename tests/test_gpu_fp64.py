@@ -168,3 +168,28 @@ def test_invalid_inputs_are_reported(tiny):
     with pytest.raises(pkg.McMp2Error) as e:
         ctx.run_steps(1, 0)  # walkers never set
     assert e.value.code == -2
+
+
+def test_initial_draw_follows_the_weight_function(tiny):
+    """set_walkers(None): positions drawn from the mixture g; per-electron mean and
+    mean squared distance from the origin match the mixture's closed forms."""
+    import math
+    m = 20000
+    ctx = pkg.Context(tiny, m, 1, pkg.MCMP2_FP64)
+    ctx.set_walkers(None, 99, 0)
+    r, _ = ctx.get_walkers()
+    pts = r.reshape(-1, 3)
+    masses, means, second = [], [], []
+    for R, (c1, z1, c2, z2) in zip(tiny.centres, tiny.weight):
+        for c, z in ((c1, z1), (c2, z2)):
+            masses.append(c * (2 * z / math.pi) ** 0.75 * (math.pi / z) ** 1.5)
+            means.append(R)
+            second.append(R @ R + 3 * 0.5 / z)
+    w = np.array(masses) / np.sum(masses)
+    mean = (w[:, None] * np.array(means)).sum(axis=0)
+    msq = float(w @ np.array(second))
+    n = len(pts)
+    sd = np.sqrt(np.maximum(msq - mean @ mean, 1e-12) / n)
+    assert np.all(np.abs(pts.mean(axis=0) - mean) < 6 * sd + 1e-12)
+    d2 = (pts ** 2).sum(axis=1)
+    assert abs(d2.mean() - msq) < 6 * d2.std() / np.sqrt(n)

@@ -121,3 +121,22 @@ def test_mixed_walk_statistics_and_checkpoint(tiny_soft):
     b = other.run_steps(90, seed)
     assert a == b
     assert a["steps"] == 210 and a["n_blocks"] == 2 and np.isfinite(a["energy"])
+
+
+@pytest.mark.parametrize("prec", [pkg.MCMP2_FP64, pkg.MCMP2_MIXED])
+def test_profile_counters_time_the_contraction_in_graph_replays(tiny_soft, prec):
+    m = 32
+    ctx = pkg.Context(tiny_soft, m, 2, prec)
+    ctx.set_walkers(None, 3, 20)
+    ctx.run_steps(2, 3)  # builds the step graph without timing
+    ctx.profile(1)
+    for _ in range(5):
+        ctx.run_steps_async(1, 3)
+    ctx.run_steps(3, 3)
+    prof = ctx.profile(0)
+    assert prof["pair_launches"] == 8
+    assert prof["launches"] >= 8 * 5
+    assert prof["pair_ms"] > 0.0
+    ctx.profile(2)
+    ctx.run_steps(2, 3)
+    assert ctx.profile(0)["pair_ms"] == 0.0
