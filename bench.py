@@ -227,6 +227,7 @@ def main():
     ctx.profile(1)
     dev_ms = time_steps(ctx, torch, args.steps, seed, flush)
     prof = ctx.profile(0)
+    ctx.profile(2)  # timing off again
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -277,6 +278,7 @@ def main():
         fctx.profile(1)
         f_ms = time_steps(fctx, torch, args.fp64_steps, seed, flush)
         fp = fctx.profile(0)
+        fctx.profile(2)
         f_pair = fp["pair_ms"] / max(1, fp["pair_launches"])
         fp64 = {"value": args.fp64_steps * samples_per_step / (f_ms / 1e3), "ms_per_step": f_ms / args.fp64_steps,
                 "pair_kernel_ms": f_pair,

@@ -191,6 +191,15 @@ typedef struct {
  * mode 2: reset them and stop timing.  out may be NULL for modes 1 and 2. */
 int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out_host);
 
+/* Test hook for the bounded waits of the tensor-core contraction (mixed form):
+ * the next contraction launch withholds its first operand copy, so its
+ * consumer's wait (limited to wait_limit_s seconds, at most 10) runs out; the
+ * kernel then stops, drains its own copies, frees tensor memory and returns,
+ * and the call that issued it reports MCMP2_ETIMEOUT.  The context stays
+ * usable.  The paper has no counterpart; this exists to test failure
+ * reporting without a device fault. */
+int mcmp2_test_stall_next(mcmp2_ctx *ctx, double wait_limit_s);
+
 /* Size of a checkpoint (walkers, displacement, step counter, statistics,
  * system digest) and its serialisation into / restoration from a host
  * buffer.  Restoring into a context with the same system and dims continues

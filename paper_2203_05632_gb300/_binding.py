@@ -74,6 +74,7 @@ SIGNATURES = {
     "mcmp2_backward": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
     "mcmp2_debug_partials": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mcmp2_profile": (_I, [_P, _I, ctypes.POINTER(ProfileCounters)]),
+    "mcmp2_test_stall_next": (_I, [_P, ctypes.c_double]),
     "mcmp2_checkpoint_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "mcmp2_pair_sum_f64_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, ctypes.c_double, _P, _P]),
     "mcmp2_checkpoint": (_I, [_P, _P, _SZ]),
@@ -256,6 +257,10 @@ class Context:
         pc = ProfileCounters()
         self._check(self.lib.mcmp2_profile(self.h, int(mode), ctypes.byref(pc) if mode == 0 else None))
         return {k: getattr(pc, k) for k, _ in pc._fields_} if mode == 0 else None
+
+    def test_stall_next(self, wait_limit_s: float):
+        """Test hook: the next contraction launch withholds its first copy (bounded wait runs out)."""
+        self._check(self.lib.mcmp2_test_stall_next(self.h, float(wait_limit_s)))
 
     def checkpoint(self) -> bytes:
         n = _SZ(0)

@@ -94,6 +94,17 @@ __device__ __forceinline__ double weight_g(const DevSystem &s, double x, double 
     return g;
 }
 
+// Records ev on st; while st is being captured into a graph the record becomes
+// an external event node, so the event can be read after each replay.
+inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, st);
+}
+
 // ---------------------------------------------------------------------------
 // Launch wrappers (defined in the kernel translation units).  All take the
 // context's stream and return cudaGetLastError() of the launch.
@@ -129,7 +140,7 @@ struct ReduceScratch {
 };
 cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tiles, double *out_slot,
                           Stats *stats, int update_stats, unsigned long long *step_to_advance,
-                          ReduceScratch *scratch, cudaStream_t st);
+                          ReduceScratch *scratch, cudaStream_t st, const int *abort_flag = nullptr);
 
 __host__ __device__ inline int pair_blocks(int m, int tile_pairs) { return (m + tile_pairs - 1) / tile_pairs; }
 __host__ __device__ inline int n_tiles_for(int m, int tile_pairs)

@@ -369,6 +369,8 @@ struct PairArgs {
     int *abort_flag;
     int m, n_tiles, nb, n_tau, n_occ, n_vir;
     double inv_lambda;
+    unsigned long long timeout_ns;  // limit of every wait
+    int withhold_first_copy;        // test hook: never issue the first stage's copy (its wait runs out)
 };
 
 __device__ __forceinline__ void pair_tile(int tile, int nb, int &bp, int &bq)
@@ -430,9 +432,17 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                 int bp, bq;
                 pair_tile(tile, args.nb, bp, bq);
                 for (int c = 0; c < chunks_per_tile; ++c) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, args.abort_flag, 1, TIMEOUT_NS)) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, args.abort_flag, 1, args.timeout_ns)) {
                         ok = false;
                         break;
+                    }
+                    if (args.withhold_first_copy && item == (int)blockIdx.x && c == 0) {
+                        // Test hook: skip this stage entirely; nothing completes its barrier.
+                        if (++stage == PR_STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                        continue;
                     }
                     const bool occ = c < n_occ_chunks;
                     const int x = (occ ? c : c - n_occ_chunks) * BK;
@@ -454,7 +464,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             }
             if (!ok)
                 for (int s = 0; s < PR_STAGES; ++s)
-                    if (issued[s]) mbar_drain(&full[s], issued_phase[s], TIMEOUT_NS);
+                    if (issued[s]) mbar_drain(&full[s], issued_phase[s], args.timeout_ns);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -464,13 +474,13 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             bool ok = true;
             const uint32_t id_pos = idesc_bf16(128, false), id_neg = idesc_bf16(128, true);
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                if (!mbar_wait(tmem_empty, tphase ^ 1u, args.abort_flag, 2, TIMEOUT_NS)) {
+                if (!mbar_wait(tmem_empty, tphase ^ 1u, args.abort_flag, 2, args.timeout_ns)) {
                     ok = false;
                     break;
                 }
                 fence_after();
                 for (int c = 0; c < chunks_per_tile; ++c) {
-                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 3, TIMEOUT_NS)) {
+                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 3, args.timeout_ns)) {
                         ok = false;
                         break;
                     }
@@ -518,7 +528,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                 tphase ^= 1u;
             }
             umma_commit(&empty[stage]);
-            mbar_drain(&empty[stage], phase, TIMEOUT_NS);
+            mbar_drain(&empty[stage], phase, args.timeout_ns);
         }
     } else {
         // ---------------- epilogue (8 warps, two per lane quarter) ----------------
@@ -534,7 +544,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
             int bp, bq;
             pair_tile(tile, args.nb, bp, bq);
-            const bool got = mbar_wait(tmem_full, ephase, args.abort_flag, 4, TIMEOUT_NS);
+            const bool got = mbar_wait(tmem_full, ephase, args.abort_flag, 4, args.timeout_ns);
             if (bar_any<1, 32 * PR_EPI_WARPS>(!got)) break;  // all epilogue warps leave together
             ephase ^= 1u;
             fence_after();
@@ -846,11 +856,16 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     std::memcpy(&pmaps.vir, plan.maps_pairs[1], sizeof(CUtensorMap));
     const int nb = pair_blocks(s.m, 16);
     const int n_tiles = nb * (nb + 1) / 2;
-    PairArgs pa{a, partials, flag, s.m, n_tiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda};
+    PairArgs pa{a, partials, flag, s.m, n_tiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda, TIMEOUT_NS, 0};
+    if (plan.withhold_once_ns) {
+        pa.withhold_first_copy = 1;
+        pa.timeout_ns = plan.withhold_once_ns;
+        plan.withhold_once_ns = 0;
+    }
     const int items = n_tiles * s.n_tau;
-    if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    if (ev) record_event(ev[0], st);
     pairs_mixed_kernel<<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
-    if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+    if (ev) record_event(ev[1], st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("mixed-form launch: ") + cudaGetErrorString(e);

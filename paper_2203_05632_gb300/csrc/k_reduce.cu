@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, c
                                                              int n_tiles, double *__restrict__ out_slot,
                                                              Stats *__restrict__ st, int update,
                                                              unsigned long long *__restrict__ step,
-                                                             ReduceScratch *__restrict__ scratch)
+                                                             ReduceScratch *__restrict__ scratch,
+                                                             const int *__restrict__ abort_flag)
 {
     __shared__ double sv[RED_THREADS], se[RED_THREADS];
     __shared__ bool last;
@@ -79,8 +80,11 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, c
     const double S = sv[0] + se[0];
     const double npairs = 0.5 * (double)m * (double)(m - 1);
     const double value = S / npairs / (double)n_tau;
-    *out_slot = value;
-    if (update) {
+    // A contraction that gave up on a wait left some partial sums unwritten:
+    // report no estimate and leave the statistics untouched.
+    const bool aborted = abort_flag && *(volatile const int *)abort_flag;
+    *out_slot = aborted ? __longlong_as_double(0x7ff8000000000000ll) : value;
+    if (update && !aborted) {
         st->last = value;
         st->steps += 1;
         kahan_add(st->all_sum, st->all_comp, value);
@@ -102,10 +106,10 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(int n_tau, int m, c
 
 cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tiles, double *out_slot,
                           Stats *stats, int update_stats, unsigned long long *step_to_advance,
-                          ReduceScratch *scratch, cudaStream_t st)
+                          ReduceScratch *scratch, cudaStream_t st, const int *abort_flag)
 {
     reduce_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(s.n_tau, s.m, partials, n_tiles, out_slot, stats, update_stats,
-                                                       step_to_advance, scratch);
+                                                       step_to_advance, scratch, abort_flag);
     return cudaGetLastError();
 }
 

@@ -494,9 +494,9 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         double *phi = ctx->at<double>(L.phi);
         CK(launch_basis<double>(S, r, B, st), "basis values");
         CK(launch_spinors_f64(S, B, phi, st), "spinor formation");
-        if (e0) CK(cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal), "event");
+        if (e0) CK(record_event(e0, st), "event");
         CK(launch_pairs_f64(S, phi, scale, a, partials, st), "pair-of-pairs tiles");
-        if (e1) CK(cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal), "event");
+        if (e1) CK(record_event(e1, st), "event");
         ctx->launches += 4;
         ctx->pair_launches += 1;
     } else {
@@ -508,7 +508,8 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         ctx->pair_launches += n_pair;
     }
     CK(launch_reduce(S, partials, L.n_tiles, out_slot, ctx->at<Stats>(L.stats), update, advance ? step : nullptr,
-                     ctx->at<ReduceScratch>(L.red), st),
+                     ctx->at<ReduceScratch>(L.red), st,
+                     ctx->precision == MCMP2_MIXED ? ctx->at<int>(L.mixed.flag) : nullptr),
        "step reduction");
     ctx->launches += 1;
     return MCMP2_OK;
@@ -584,6 +585,15 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
     // One step is captured once into a CUDA graph (its kernels read the step
     // counter from device memory, so the graph is the same for every step)
     // and replayed n times on the caller's stream.
+    if (ctx->precision == MCMP2_MIXED && ctx->mixed.withhold_once_ns && n > 0) {
+        // A pending test stall applies to one directly issued step.
+        CK(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta, &stats->accepted,
+                             ctx->at<double>(L.a), st),
+           "metropolis");
+        const int rc = step_integrand(ctx, r, nullptr, seed, ctx->at<double>(L.per_step), 1, true, true);
+        if (rc) return rc;
+        --n;
+    }
     if (n > 0 && (!ctx->graph || ctx->graph_seed != seed || ctx->graph_delta != ctx->delta ||
                   ctx->graph_timing != ctx->timing)) {
         ctx->drop_graph();
@@ -841,6 +851,16 @@ int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out)
         }
     }
     out->pair_ms = ms + ctx->graph_pair_ms;
+    return MCMP2_OK;
+}
+
+int mcmp2_test_stall_next(mcmp2_ctx *ctx, double wait_limit_s)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (ctx->precision != MCMP2_MIXED) return ctx->fail(MCMP2_EUNSUPPORTED, "the hook applies to the mixed form");
+    if (!(wait_limit_s > 0.0) || wait_limit_s > 10.0) return ctx->fail(MCMP2_EINVAL, "wait limit must be in (0, 10] s");
+    ctx->mixed.withhold_once_ns = (unsigned long long)(wait_limit_s * 1e9);
+    ctx->drop_graph();  // the next step is issued directly, not replayed
     return MCMP2_OK;
 }
 

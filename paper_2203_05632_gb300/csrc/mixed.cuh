@@ -23,6 +23,7 @@ struct MixedLayout {
 // Host-side state: tensor maps (8 for spinor formation, 2 for the contraction).
 struct MixedPlan {
     bool ready = false;
+    unsigned long long withhold_once_ns = 0;  // test hook for the bounded-wait path (see mcmp2_test_stall_next)
     alignas(64) unsigned char maps_spinor[8][128];
     alignas(64) unsigned char maps_pairs[2][128];
 };

@@ -13,10 +13,16 @@ holds the host-side bookkeeping:
 * ``gather_and_combine`` — collect every rank's result over a
   ``torch.distributed`` process group at the end of a run and combine them.
   Ranks that failed pass ``None`` and are left out.
+* ``write_result`` / ``combine_directory`` — the fault-tolerant path: each
+  replica writes its result file atomically when it finishes (or at each
+  checkpoint); the combination reads whatever the surviving replicas wrote,
+  so a replica that died leaves nothing behind and is simply absent.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 
 
 def combine(results):
@@ -70,3 +76,33 @@ def gather_and_combine(result, group=None):
     gathered = [None] * world
     dist.all_gather_object(gathered, result, group=group)
     return combine(gathered), gathered
+
+
+def write_result(directory, replica, result):
+    """Atomically write one replica's result (a dict) as <directory>/replica-<id>.json."""
+    os.makedirs(directory, exist_ok=True)
+    final = os.path.join(directory, f"replica-{int(replica)}.json")
+    tmp = final + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(result, f)
+        f.flush()
+        os.fsync(f.fileno())
+    os.replace(tmp, final)
+    return final
+
+
+def combine_directory(directory):
+    """Combine the results of the replicas that wrote one; unreadable files are skipped."""
+    results = {}
+    if os.path.isdir(directory):
+        for name in sorted(os.listdir(directory)):
+            if not (name.startswith("replica-") and name.endswith(".json")):
+                continue
+            try:
+                with open(os.path.join(directory, name)) as f:
+                    results[name] = json.load(f)
+            except (OSError, ValueError):
+                continue
+    out = combine(results.values())
+    out["replicas"] = sorted(results)
+    return out

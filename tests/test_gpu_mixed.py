@@ -140,3 +140,16 @@ def test_profile_counters_time_the_contraction_in_graph_replays(tiny_soft, prec)
     ctx.profile(2)
     ctx.run_steps(2, 3)
     assert ctx.profile(0)["pair_ms"] == 0.0
+
+
+def test_timing_mode_outside_graphs(tiny):
+    """Replay calls issue kernels directly; timing them must work as well."""
+    m = 16
+    r = synthetic.walker_positions(tiny.centres, 2, m, seed=8)
+    tau = synthetic.imaginary_times(2.0, 2, 1, seed=9)
+    for prec in (pkg.MCMP2_FP64, pkg.MCMP2_MIXED):
+        ctx = pkg.Context(tiny, m, 1, prec)
+        ctx.profile(1)
+        ctx.eval_fixed(r, tau)
+        prof = ctx.profile(0)
+        assert prof["pair_launches"] == 2 and prof["pair_ms"] > 0.0

@@ -77,3 +77,29 @@ def test_gather_over_gloo_two_ranks(failed_rank):
         assert gathered == results
         assert combined["n_replicas"] == (2 if failed_rank is None else 1)
         assert combined["energy"] == pytest.approx(want["energy"])
+
+
+def _replica_process(directory, replica, energy, error, crash):
+    from paper_2203_05632_gb300 import replicas as R
+    if crash:
+        raise SystemExit(3)  # dies before writing anything
+    R.write_result(directory, replica, {"energy": energy, "error": error, "steps": 1000})
+
+
+def test_surviving_replicas_are_combined_after_a_crash(tmp_path):
+    """A replica that dies leaves no result; the others are combined (the paper's
+    weighted average over surviving processors)."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    specs = [(0, -1.00, 0.05, False), (1, -1.10, 0.10, True), (2, -0.95, 0.05, False)]
+    procs = [ctx.Process(target=_replica_process, args=(str(tmp_path), *s)) for s in specs]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert [p.exitcode for p in procs] == [0, 3, 0]
+    (tmp_path / "replica-9.json").write_text("{truncated")  # a torn file is ignored
+    out = replicas.combine_directory(str(tmp_path))
+    assert out["n_replicas"] == 2
+    assert out["energy"] == pytest.approx(-0.975)
+    assert out["error"] == pytest.approx(0.05 / math.sqrt(2))
