@@ -102,8 +102,8 @@ constexpr int SP_STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo
 constexpr int SP_THREADS = 192;                 // TMA warp, MMA warp, 4 epilogue warps
 constexpr int SP_TMEM_COLS = 256;               // two 128-column accumulators
 constexpr int SP_MAX_TAU = 64;                  // scale staging capacity (the API limits n_tau to 64)
-constexpr int SP_ROW_BYTES = 144;               // staged row: 64 BF16 (128 B) + 16 B pad against bank conflicts
-constexpr int SP_WARP_STAGE = 4 * 32 * SP_ROW_BYTES;  // 4 planes x 32 rows per epilogue warp
+constexpr int SP_ROW_BYTES = 528;               // staged row: 4 chunks x 4 planes x 16 BF16 (512 B) + 16 B pad
+constexpr int SP_WARP_STAGE = 32 * SP_ROW_BYTES;  // 32 rows per epilogue warp
 constexpr int SP_BARS_OFF = SP_STAGES * SP_STAGE_BYTES;
 constexpr int SP_SCALE_OFF = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16;
 constexpr int SP_WSTAGE_OFF = SP_SCALE_OFF + SP_MAX_TAU * 64 * 4;
@@ -115,8 +115,8 @@ struct SpinorMaps {
 
 struct SpinorArgs {
     const float *scale;   // [n_tau][n_orb]
-    __nv_bfloat16 *occ;   // [n_tau][4][rows][k_occ_pad]
-    __nv_bfloat16 *vir;   // [n_tau][4][rows][k_vir_pad]
+    __nv_bfloat16 *occ;   // [n_tau][rows][k_occ_pad / 16][4 planes][16]
+    __nv_bfloat16 *vir;   // [n_tau][rows][k_vir_pad / 16][4 planes][16]
     int *abort_flag;
     int P, nl, n_mt, n_kb, n_kb_occ, n_occ, n_vir, n_orb, n_tau, rows, k_occ_pad, k_vir_pad;
 };
@@ -251,9 +251,10 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         }
     } else {
         // Epilogue: each lane owns one position row of the tile.  For every time
-        // the warp stages its 32 rows x 64 orbitals of the 4 planes in shared
-        // memory, then writes them as whole 128-byte row segments (8 lanes per
-        // row), so each store instruction touches 4 lines instead of 32.
+        // the warp stages its 32 rows x 64 orbitals in shared memory in the
+        // contraction's operand order (per 16-orbital chunk: re_hi, re_lo, im_hi,
+        // im_lo, 32 B each), then writes each row's 512 contiguous bytes with one
+        // 16-byte store per lane.
         const int ew = warp - 2;
         const int quarter = warp & 3;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             const int k_first = (occ ? 0 : args.n_occ) + kl * 64;  // absolute index of the block's first orbital
             const int k_end = occ ? args.n_occ : args.n_orb;       // one past the region's last orbital
             __nv_bfloat16 *planes = occ ? args.occ : args.vir;
-            const size_t plane_elems = (size_t)args.rows * kpad;
+            const size_t time_elems = (size_t)args.rows * 4 * kpad;  // one time's operand rows
             for (int i = threadIdx.x - 64; i < 64 * args.n_tau; i += 128) {
                 const int t = i >> 6, k = k_first + (i & 63);
                 sscale[i] = k < k_end ? args.scale[(size_t)t * args.n_orb + k] : 0.f;
@@ -301,36 +302,27 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                         rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
                         il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
                     }
-                    unsigned char *myrow = wstage + lane * SP_ROW_BYTES + 32 * j;
-                    uint4 *d0 = reinterpret_cast<uint4 *>(myrow), *d1 = reinterpret_cast<uint4 *>(myrow + 32 * SP_ROW_BYTES);
-                    uint4 *d2 = reinterpret_cast<uint4 *>(myrow + 64 * SP_ROW_BYTES);
-                    uint4 *d3 = reinterpret_cast<uint4 *>(myrow + 96 * SP_ROW_BYTES);
-                    d0[0] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                    d0[1] = make_uint4(rh[4], rh[5], rh[6], rh[7]);
-                    d1[0] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                    d1[1] = make_uint4(rl[4], rl[5], rl[6], rl[7]);
-                    d2[0] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                    d2[1] = make_uint4(ih[4], ih[5], ih[6], ih[7]);
-                    d3[0] = make_uint4(il[0], il[1], il[2], il[3]);
-                    d3[1] = make_uint4(il[4], il[5], il[6], il[7]);
+                    uint4 *d = reinterpret_cast<uint4 *>(wstage + lane * SP_ROW_BYTES + 128 * j);
+                    d[0] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                    d[1] = make_uint4(rh[4], rh[5], rh[6], rh[7]);
+                    d[2] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                    d[3] = make_uint4(rl[4], rl[5], rl[6], rl[7]);
+                    d[4] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                    d[5] = make_uint4(ih[4], ih[5], ih[6], ih[7]);
+                    d[6] = make_uint4(il[0], il[1], il[2], il[3]);
+                    d[7] = make_uint4(il[4], il[5], il[6], il[7]);
                 }
                 __syncwarp();
-                const int chunk = lane & 7;
-#pragma unroll
-                for (int pl = 0; pl < 4; ++pl)
-#pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const int r_in = 4 * it + (lane >> 3);
-                        const int x = mt * 128 + 32 * quarter + r_in;
-                        if (x < args.P) {
-                            const uint4 v =
-                                *reinterpret_cast<const uint4 *>(wstage + pl * 32 * SP_ROW_BYTES + r_in * SP_ROW_BYTES +
-                                                                 16 * chunk);
-                            __nv_bfloat16 *dst = planes + ((size_t)t * 4 + pl) * plane_elems + (size_t)(4 * x + c4) * kpad +
-                                                 kl * 64 + 8 * chunk;
-                            *reinterpret_cast<uint4 *>(dst) = v;
-                        }
+#pragma unroll 4
+                for (int it = 0; it < 32; ++it) {
+                    const int x = mt * 128 + 32 * quarter + it;
+                    if (x < args.P) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(wstage + it * SP_ROW_BYTES + 16 * lane);
+                        __nv_bfloat16 *dst =
+                            planes + (size_t)t * time_elems + (size_t)(4 * x + c4) * (4 * kpad) + kl * 256 + 8 * lane;
+                        *reinterpret_cast<uint4 *>(dst) = v;
                     }
+                }
                 __syncwarp();
             }
             fence_before();
@@ -350,17 +342,44 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
 // ===========================================================================
 // 3. Pair-of-pairs contraction with the trace epilogue
 // ===========================================================================
-constexpr int PR_STAGES = 3;
-constexpr int PR_STAGE_BYTES = 8 * TILE_BYTES;  // A: re_hi, re_lo, im_hi, im_lo; B: the same
-constexpr int PR_EPI_WARPS = 8;                 // two per tensor-memory lane quarter
+// Operand rows: one row per (position x, component c), row 4x + c, holding
+// for each 16-orbital chunk the four split planes re_hi, re_lo, im_hi, im_lo
+// side by side (128 B), so one 128-byte-swizzled TMA box of 128 rows brings
+// all four planes of a chunk and the MMA selects a plane by a 32-byte offset.
+//
+// Work item = (tile of 16 x 16 walker pairs, time).  Per item the tensor
+// cores accumulate G- (K = n_occ) and then G+ (K = n_vir) as 128 x 128
+// complex blocks (rows 8p + 4e + c of the p-pairs, columns 8q + 4e' + d of
+// the q-pairs) in one 256-column half of tensor memory.  Two epilogue
+// groups take alternate items, each with its own half: while one group
+// traces item i, the MMA warp fills the other half with item i+1.  G- is
+// accumulated first in the same columns; its group copies the like-electron
+// blocks G-(ep, eq) (the only G- blocks the trace form needs) to shared
+// memory at once, which frees the columns for G+.  With PR_GM_PACKED they
+// are kept there as 24-bit floats (FP32 rounded to 15 stored significand
+// bits, relative error at most 2^-16, about the error the split BF16
+// products already carry), which leaves room for a fourth operand stage.
+constexpr int PR_BK = 16;                          // orbitals per chunk (one stage)
+constexpr int PR_TILE_BYTES = 128 * 4 * PR_BK * 2; // 128 rows x (4 planes x 16 BF16) = 16 KB
+constexpr bool PR_GM_PACKED = true;                // G- kept as 24-bit floats
+constexpr int PR_STAGES = PR_GM_PACKED ? 4 : 3;
+constexpr int PR_STAGE_BYTES = 2 * PR_TILE_BYTES;  // A chunk, then B chunk
+constexpr int PR_GROUPS = 2;
+constexpr int PR_GROUP_WARPS = 8;                  // two per tensor-memory lane quarter
+constexpr int PR_EPI_WARPS = PR_GROUPS * PR_GROUP_WARPS;
 constexpr int PR_THREADS = 64 + 32 * PR_EPI_WARPS;
-constexpr int PR_TMEM_COLS = 512;               // G+ re | G+ im | G- re | G- im
-constexpr int PR_BARS_OFF = PR_STAGES * PR_STAGE_BYTES;
-constexpr int PR_RED_OFF = PR_BARS_OFF + (2 * PR_STAGES + 2) * 8 + 16;
-constexpr int PR_SMEM = PR_RED_OFF + 32 * 8 + 1024;
+constexpr int PR_TMEM_COLS = 512;                  // per group: re | im of 128 columns
+// G- like blocks of one item: [16 q][3][128 rows] uint2 (8 x 24 bit) or [16 q][2][128 rows] float4
+constexpr int PR_GM_BYTES = PR_GM_PACKED ? 16 * 3 * 128 * 8 : 16 * 2 * 128 * 16;
+constexpr int PR_GM_OFF = PR_STAGES * PR_STAGE_BYTES;
+constexpr int PR_BARS_OFF = PR_GM_OFF + PR_GROUPS * PR_GM_BYTES;
+constexpr int PR_RED_OFF = PR_BARS_OFF + 192;      // barriers + tensor-memory slot
+constexpr int PR_SMEM = PR_RED_OFF + PR_GROUPS * 32 * 8 + 1024;
+static_assert(PR_SMEM <= 232448, "contraction kernel exceeds the shared memory of one CTA");
+static_assert((2 * PR_STAGES + 4 * PR_GROUPS) * 8 + 4 <= 192, "barrier block too small");
 
 struct PairMaps {
-    CUtensorMap occ, vir;  // 3-D: (orbital, row, 4 tau + plane)
+    CUtensorMap occ, vir;  // 3-D: (chunk x plane x orbital, row, tau), 64 x 128 boxes, 128-byte swizzle
 };
 
 struct PairArgs {
@@ -384,6 +403,54 @@ __device__ __forceinline__ void pair_tile(int tile, int nb, int &bp, int &bq)
     bq = b + k;
 }
 
+__device__ __forceinline__ int pr_chunks(int k) { return (k + PR_BK - 1) / PR_BK; }
+
+// Four floats rounded to 24 bits (sign, exponent, 15 stored significand
+// bits; round half away from zero on the magnitude) packed into three words.
+__device__ __forceinline__ uint32_t r24(float x) { return (__float_as_uint(x) + 0x80u) >> 8; }
+__device__ __forceinline__ uint3 pack24(float a, float b, float c, float d)
+{
+    const uint32_t A = r24(a), B = r24(b), C = r24(c), D = r24(d);
+    return make_uint3(A | (B << 24), (B >> 8) | (C << 16), (C >> 16) | (D << 8));
+}
+__device__ __forceinline__ void unpack24(uint32_t w0, uint32_t w1, uint32_t w2, float &a, float &b, float &c, float &d)
+{
+    a = __uint_as_float(w0 << 8);
+    b = __uint_as_float(__byte_perm(w0, w1, 0x5433) & 0xFFFFFF00u);
+    c = __uint_as_float(__byte_perm(w1, w2, 0x4322) & 0xFFFFFF00u);
+    d = __uint_as_float(w2 & 0xFFFFFF00u);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle (8 rows x 128 B
+// atoms, 1024 B between 8-row groups), SM100 descriptor version 1.  The
+// start address may sit 32, 64 or 96 B into a 1024-byte-aligned tile: the
+// swizzle is applied to the absolute address, which selects a 16-element
+// slice of every row.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+    return d;
+}
+
+// OR of a predicate over the 256 threads of epilogue group g (named barriers 1 and 2).
+__device__ __forceinline__ bool group_any(int g, bool v)
+{
+    return g == 0 ? bar_any<1, 32 * PR_GROUP_WARPS>(v) : bar_any<2, 32 * PR_GROUP_WARPS>(v);
+}
+
+__device__ __forceinline__ void group_sync(int g)
+{
+    if (g == 0)
+        bar_sync<1, 32 * PR_GROUP_WARPS>();
+    else
+        bar_sync<2, 32 * PR_GROUP_WARPS>();
+}
+
 __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid_constant__ PairMaps maps,
                                                                     const PairArgs args)
 {
@@ -392,14 +459,16 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + PR_BARS_OFF);
     uint64_t *empty = full + PR_STAGES;
-    uint64_t *tmem_full = empty + PR_STAGES;
-    uint64_t *tmem_empty = tmem_full + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 1);
-    double *red = reinterpret_cast<double *>(smem + PR_RED_OFF);
+    uint64_t *mfull = empty + PR_STAGES;  // [group] G- accumulated
+    uint64_t *munl = mfull + PR_GROUPS;   // [group] G- copied out (8 warps)
+    uint64_t *pfull = munl + PR_GROUPS;   // [group] G+ accumulated
+    uint64_t *pfree = pfull + PR_GROUPS;  // [group] columns free again (8 warps)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pfree + PR_GROUPS);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_occ_chunks = n_chunks(args.n_occ), n_vir_chunks = n_chunks(args.n_vir);
-    const int chunks_per_tile = n_occ_chunks + n_vir_chunks;
+    const int n_occ_chunks = pr_chunks(args.n_occ), n_vir_chunks = pr_chunks(args.n_vir);
+    const int n_occ_stages = n_occ_chunks;
+    const int stages_per_tile = n_occ_chunks + n_vir_chunks;
     const int n_items = args.n_tiles * args.n_tau;
 
     if (threadIdx.x == 0) {
@@ -407,8 +476,12 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(tmem_full, 1);
-        mbar_init(tmem_empty, PR_EPI_WARPS);
+        for (int g = 0; g < PR_GROUPS; ++g) {
+            mbar_init(&mfull[g], 1);
+            mbar_init(&munl[g], PR_GROUP_WARPS);
+            mbar_init(&pfull[g], 1);
+            mbar_init(&pfree[g], PR_GROUP_WARPS);
+        }
         mbar_init_fence();
     }
     if (warp == 1) tmem_alloc(tmem_slot, PR_TMEM_COLS);
@@ -431,8 +504,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                 const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
                 int bp, bq;
                 pair_tile(tile, args.nb, bp, bq);
-                for (int c = 0; c < chunks_per_tile; ++c) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, args.abort_flag, 1, args.timeout_ns)) {
+                for (int c = 0; c < stages_per_tile; ++c) {
+                    if (!mbar_wait_fast(&empty[stage], phase ^ 1u, args.abort_flag, 1, args.timeout_ns)) {
                         ok = false;
                         break;
                     }
@@ -444,16 +517,13 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                         }
                         continue;
                     }
-                    const bool occ = c < n_occ_chunks;
-                    const int x = (occ ? c : c - n_occ_chunks) * BK;
+                    const bool occ = c < n_occ_stages;
+                    const int x = (occ ? c : c - n_occ_stages) * 4 * PR_BK;
                     const CUtensorMap *mp = occ ? &maps.occ : &maps.vir;
                     unsigned char *st = smem + stage * PR_STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[stage], PR_STAGE_BYTES);
-#pragma unroll
-                    for (int pl = 0; pl < 4; ++pl) {
-                        tma_load_3d(st + pl * TILE_BYTES, mp, &full[stage], x, bp * 128, 4 * t + pl);
-                        tma_load_3d(st + (4 + pl) * TILE_BYTES, mp, &full[stage], x, bq * 128, 4 * t + pl);
-                    }
+                    tma_load_3d(st, mp, &full[stage], x, bp * 128, t);
+                    tma_load_3d(st + PR_TILE_BYTES, mp, &full[stage], x, bq * 128, t);
                     issued[stage] = 1;
                     issued_phase[stage] = phase;
                     if (++stage == PR_STAGES) {
@@ -470,53 +540,62 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             int stage = 0;
-            uint32_t phase = 0, tphase = 0;
+            uint32_t phase = 0;
+            uint32_t use[PR_GROUPS] = {0, 0};  // parity of each group's uses so far
             bool ok = true;
             const uint32_t id_pos = idesc_bf16(128, false), id_neg = idesc_bf16(128, true);
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                if (!mbar_wait(tmem_empty, tphase ^ 1u, args.abort_flag, 2, args.timeout_ns)) {
+            // Descriptors of stage 0; stage s adds s * PR_STAGE_BYTES to the start-address
+            // field (address >> 4 in the low 14 bits, no carry for addresses below 256 KB).
+            // Keeping this loop short matters: the tensor pipe drains while it runs.
+            const uint32_t base0 = smem_u32(smem);
+            const uint64_t arh0 = sdesc_sw128(base0 + 0), arl0 = sdesc_sw128(base0 + 32);
+            const uint64_t aih0 = sdesc_sw128(base0 + 64), ail0 = sdesc_sw128(base0 + 96);
+            constexpr uint32_t BOFF = PR_TILE_BYTES;
+            const uint64_t brh0 = sdesc_sw128(base0 + BOFF + 0), brl0 = sdesc_sw128(base0 + BOFF + 32);
+            const uint64_t bih0 = sdesc_sw128(base0 + BOFF + 64), bil0 = sdesc_sw128(base0 + BOFF + 96);
+            int li = 0;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++li) {
+                const int g = li & 1;
+                const uint32_t d_re = tmem + 256u * g, d_im = d_re + 128u;
+                if (!mbar_wait_fast(&pfree[g], use[g] ^ 1u, args.abort_flag, 2, args.timeout_ns)) {
                     ok = false;
                     break;
                 }
                 fence_after();
-                for (int c = 0; c < chunks_per_tile; ++c) {
-                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 3, args.timeout_ns)) {
+                for (int c = 0; c < stages_per_tile; ++c) {
+                    if (c == n_occ_stages) {
+                        // G- complete: hand it to the group, then reuse the columns for G+.
+                        umma_commit(&mfull[g]);
+                        if (!mbar_wait_fast(&munl[g], use[g], args.abort_flag, 5, args.timeout_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                    }
+                    if (!mbar_wait_fast(&full[stage], phase, args.abort_flag, 3, args.timeout_ns)) {
                         ok = false;
                         break;
                     }
                     fence_after();
-                    const bool occ = c < n_occ_chunks;
-                    const int cc = occ ? c : c - n_occ_chunks;
-                    const int kvalid = (occ ? args.n_occ : args.n_vir) - cc * BK;
-                    const int ksteps = kvalid >= BK ? BK / 16 : (kvalid + 15) / 16;
-                    const uint32_t d_re = tmem + (occ ? 256u : 0u), d_im = d_re + 128u;
-                    const uint32_t base = smem_u32(smem + stage * PR_STAGE_BYTES);
-                    for (int ks = 0; ks < ksteps; ++ks) {
-                        const uint32_t off = ks * 32;
-                        const uint64_t arh = sdesc_sw64(base + 0 * TILE_BYTES + off);
-                        const uint64_t arl = sdesc_sw64(base + 1 * TILE_BYTES + off);
-                        const uint64_t aih = sdesc_sw64(base + 2 * TILE_BYTES + off);
-                        const uint64_t ail = sdesc_sw64(base + 3 * TILE_BYTES + off);
-                        const uint64_t brh = sdesc_sw64(base + 4 * TILE_BYTES + off);
-                        const uint64_t brl = sdesc_sw64(base + 5 * TILE_BYTES + off);
-                        const uint64_t bih = sdesc_sw64(base + 6 * TILE_BYTES + off);
-                        const uint64_t bil = sdesc_sw64(base + 7 * TILE_BYTES + off);
-                        const uint32_t acc = (cc == 0 && ks == 0) ? 0u : 1u;
-                        // Re G += Xr Yr^T + Xi Yi^T
-                        umma(d_re, arh, brh, id_pos, acc);
-                        umma(d_re, arh, brl, id_pos, 1u);
-                        umma(d_re, arl, brh, id_pos, 1u);
-                        umma(d_re, aih, bih, id_pos, 1u);
-                        umma(d_re, aih, bil, id_pos, 1u);
-                        umma(d_re, ail, bih, id_pos, 1u);
-                        // Im G += Xi Yr^T - Xr Yi^T
-                        umma(d_im, aih, brh, id_pos, acc);
-                        umma(d_im, aih, brl, id_pos, 1u);
-                        umma(d_im, ail, brh, id_pos, 1u);
-                        umma(d_im, arh, bih, id_neg, 1u);
-                        umma(d_im, arh, bil, id_neg, 1u);
-                        umma(d_im, arl, bih, id_neg, 1u);
-                    }
+                    const uint64_t so = (uint64_t)(stage * (PR_STAGE_BYTES >> 4));
+                    const uint64_t arh = arh0 + so, arl = arl0 + so, aih = aih0 + so, ail = ail0 + so;
+                    const uint64_t brh = brh0 + so, brl = brl0 + so, bih = bih0 + so, bil = bil0 + so;
+                    const uint32_t acc = (c == 0 || c == n_occ_stages) ? 0u : 1u;
+                    // Re G += Xr Yr^T + Xi Yi^T and Im G += Xi Yr^T - Xr Yi^T, alternating
+                    // between the two accumulators.  (Straight-line code: the issue loop
+                    // must stay short, the tensor pipe drains while it runs.)
+                    umma(d_re, arh, brh, id_pos, acc);
+                    umma(d_im, aih, brh, id_pos, acc);
+                    umma(d_re, arh, brl, id_pos, 1u);
+                    umma(d_im, aih, brl, id_pos, 1u);
+                    umma(d_re, arl, brh, id_pos, 1u);
+                    umma(d_im, ail, brh, id_pos, 1u);
+                    umma(d_re, aih, bih, id_pos, 1u);
+                    umma(d_im, arh, bih, id_neg, 1u);
+                    umma(d_re, aih, bil, id_pos, 1u);
+                    umma(d_im, arh, bil, id_neg, 1u);
+                    umma(d_re, ail, bih, id_pos, 1u);
+                    umma(d_im, arl, bih, id_neg, 1u);
                     umma_commit(&empty[stage]);
                     if (++stage == PR_STAGES) {
                         stage = 0;
@@ -524,53 +603,109 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                     }
                 }
                 if (!ok) break;
-                umma_commit(tmem_full);
-                tphase ^= 1u;
+                umma_commit(&pfull[g]);
+                use[g] ^= 1u;
             }
             umma_commit(&empty[stage]);
             mbar_drain(&empty[stage], phase, args.timeout_ns);
         }
     } else {
-        // ---------------- epilogue (8 warps, two per lane quarter) ----------------
+        // ---------------- epilogue: two groups of 8 warps, alternate items ----------------
         const int ew = warp - 2;
+        const int g = ew / PR_GROUP_WARPS;
+        const int gw = ew - g * PR_GROUP_WARPS;
         const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
-        const int qhalf = ew >> 2;     // q-pairs 8*qhalf .. +7 of the tile
+        const int qhalf = gw >> 2;     // q-pairs 8*qhalf .. +7 of the tile
         const int row = 32 * quarter + lane;
         const int p_local = row >> 3, e = (row >> 2) & 1, c = lane & 3;
         const int gbase = lane & ~7;
-        const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
-        uint32_t ephase = 0;
-        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + 256u * g;
+        unsigned char *gm = smem + PR_GM_OFF + g * PR_GM_BYTES;
+        double *red = reinterpret_cast<double *>(smem + PR_RED_OFF) + 32 * g;
+        uint32_t ph = 0;
+        for (int item = blockIdx.x + g * gridDim.x; item < n_items; item += PR_GROUPS * gridDim.x) {
             const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
             int bp, bq;
             pair_tile(tile, args.nb, bp, bq);
-            const bool got = mbar_wait(tmem_full, ephase, args.abort_flag, 4, args.timeout_ns);
-            if (bar_any<1, 32 * PR_EPI_WARPS>(!got)) break;  // all epilogue warps leave together
-            ephase ^= 1u;
+            // (1) G- like-electron blocks of this lane's row -> shared memory: for q, the
+            //     four entries G-(row, 8q + 4e + d) in the order re 0, im 0, re 1, im 1 |
+            //     re 2, im 2, re 3, im 3, as two float4 or, packed to 24 bits, three uint2.
+            const bool got_m = mbar_wait(&mfull[g], ph, args.abort_flag, 4, args.timeout_ns);
+            if (group_any(g, !got_m)) break;  // the group leaves together
+            fence_after();
+#pragma unroll 1
+            for (int qb = 0; qb < 4; ++qb) {
+                const int q0 = 8 * qhalf + 2 * qb;
+                float vr[16], vi[16];
+                tmem_ld<16>(lane_addr + 8u * q0, vr);
+                tmem_ld<16>(lane_addr + 128u + 8u * q0, vi);
+                tmem_wait_ld();
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                    float o_r[4], o_i[4];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        o_r[d] = e ? vr[8 * qq + 4 + d] : vr[8 * qq + d];
+                        o_i[d] = e ? vi[8 * qq + 4 + d] : vi[8 * qq + d];
+                    }
+                    const int q = q0 + qq;
+                    if constexpr (PR_GM_PACKED) {
+                        uint2 *gp = reinterpret_cast<uint2 *>(gm);
+                        const uint3 u = pack24(o_r[0], o_i[0], o_r[1], o_i[1]);
+                        const uint3 v = pack24(o_r[2], o_i[2], o_r[3], o_i[3]);
+                        gp[(3 * q + 0) * 128 + row] = make_uint2(u.x, u.y);
+                        gp[(3 * q + 1) * 128 + row] = make_uint2(u.z, v.x);
+                        gp[(3 * q + 2) * 128 + row] = make_uint2(v.y, v.z);
+                    } else {
+                        float4 *gf = reinterpret_cast<float4 *>(gm);
+                        gf[(2 * q + 0) * 128 + row] = make_float4(o_r[0], o_i[0], o_r[1], o_i[1]);
+                        gf[(2 * q + 1) * 128 + row] = make_float4(o_r[2], o_i[2], o_r[3], o_i[3]);
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&munl[g]);
+            // (2) traces once G+ is in the same columns.
+            const bool got_p = mbar_wait(&pfull[g], ph, args.abort_flag, 6, args.timeout_ns);
+            if (group_any(g, !got_p)) break;
+            ph ^= 1u;
             fence_after();
             const int p = bp * 16 + p_local;
             // a_q of the tile's 16 q-pairs, one per lane (lane & 15), fetched by shuffle below.
             const int q_lane = bq * 16 + (lane & 15);
             const double a_lane = q_lane < args.m ? args.a[q_lane] : 0.0;
             double acc = 0.0;  // sum over this warp's q of Re f_pq a_q
+#pragma unroll 1
             for (int qb = 0; qb < 4; ++qb) {
                 const int q0 = 8 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
-                float gpr[16], gpi[16], gmr[16], gmi[16];
-                const uint32_t col = 8u * q0;
-                tmem_ld<16>(lane_addr + col, gpr);
-                tmem_ld<16>(lane_addr + 128u + col, gpi);
-                tmem_ld<16>(lane_addr + 256u + col, gmr);
-                tmem_ld<16>(lane_addr + 384u + col, gmi);
+                float gpr[16], gpi[16];
+                tmem_ld<16>(lane_addr + 8u * q0, gpr);
+                tmem_ld<16>(lane_addr + 128u + 8u * q0, gpi);
                 tmem_wait_ld();
 #pragma unroll
                 for (int qq = 0; qq < 2; ++qq) {
                     // This lane holds row c of G-(xe, ye) [own], G+(xe, ye) [dia], G+(xe, y(1-e)) [off].
-                    float own_r[4], own_i[4], dia_r[4], dia_i[4], off_r[4], off_i[4];
+                    const int ql = q0 + qq;
+                    float own_r[4], own_i[4];
+                    if constexpr (PR_GM_PACKED) {
+                        const uint2 *gp = reinterpret_cast<const uint2 *>(gm);
+                        const uint2 w0 = gp[(3 * ql + 0) * 128 + row];
+                        const uint2 w1 = gp[(3 * ql + 1) * 128 + row];
+                        const uint2 w2 = gp[(3 * ql + 2) * 128 + row];
+                        unpack24(w0.x, w0.y, w1.x, own_r[0], own_i[0], own_r[1], own_i[1]);
+                        unpack24(w1.y, w2.x, w2.y, own_r[2], own_i[2], own_r[3], own_i[3]);
+                    } else {
+                        const float4 *gf = reinterpret_cast<const float4 *>(gm);
+                        const float4 m0 = gf[(2 * ql + 0) * 128 + row];
+                        const float4 m1 = gf[(2 * ql + 1) * 128 + row];
+                        own_r[0] = m0.x; own_i[0] = m0.y; own_r[1] = m0.z; own_i[1] = m0.w;
+                        own_r[2] = m1.x; own_i[2] = m1.y; own_r[3] = m1.z; own_i[3] = m1.w;
+                    }
+                    float dia_r[4], dia_i[4], off_r[4], off_i[4];
 #pragma unroll
                     for (int d = 0; d < 4; ++d) {  // constant indices keep the arrays in registers
                         const int i0 = 8 * qq + d, i1 = 8 * qq + 4 + d;
-                        own_r[d] = e ? gmr[i1] : gmr[i0];
-                        own_i[d] = e ? gmi[i1] : gmi[i0];
                         dia_r[d] = e ? gpr[i1] : gpr[i0];
                         dia_i[d] = e ? gpi[i1] : gpi[i0];
                         off_r[d] = e ? gpr[i0] : gpr[i1];
@@ -618,7 +753,6 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                     xr += __shfl_xor_sync(0xffffffffu, xr, 1);
                     xr += __shfl_xor_sync(0xffffffffu, xr, 2);
                     xr += __shfl_xor_sync(0xffffffffu, xr, 4);
-                    const int ql = q0 + qq;
                     const int q = bq * 16 + ql;
                     const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
                     const bool valid = p < args.m && q < args.m && (bp < bq || p_local < ql);
@@ -627,15 +761,15 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tmem_empty);
+            if (lane == 0) mbar_arrive(&pfree[g]);
             if ((lane & 7) == 0) red[16 * qhalf + 4 * quarter + (lane >> 3)] = (p < args.m) ? acc * args.a[p] : 0.0;
-            bar_sync<1, 32 * PR_EPI_WARPS>();
-            if (ew == 0 && lane == 0) {
+            group_sync(g);
+            if (gw == 0 && lane == 0) {
                 double sum = 0.0;
                 for (int j = 0; j < 32; ++j) sum += red[j];
                 args.partials[(size_t)t * args.n_tiles + tile] = sum * args.inv_lambda;
             }
-            bar_sync<1, 32 * PR_EPI_WARPS>();
+            group_sync(g);
         }
     }
     fence_before();
@@ -682,19 +816,21 @@ float bf2f(uint16_t h)
     return f;
 }
 
-// 2-D (or 3-D) BF16 tensor map with 64-byte swizzle and a 32 x 128 box.
-int encode(void *out, void *addr, int rank, const cuuint64_t *dims, const cuuint64_t *strides, std::string &err)
+// 2-D (or 3-D) BF16 tensor map with a box_k x 128 box: 32 elements with the 64-byte swizzle
+// (spinor formation), or 64 with the 128-byte swizzle (contraction).
+int encode(void *out, void *addr, int rank, const cuuint64_t *dims, const cuuint64_t *strides, std::string &err,
+           int box_k = BK, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_64B)
 {
     auto enc = encode_fn();
     if (!enc) {
         err = "cuTensorMapEncodeTiled is not available from the driver";
         return MCMP2_EUNSUPPORTED;
     }
-    const cuuint32_t box[3] = {(cuuint32_t)BK, 128u, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)box_k, 128u, 1u};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap map;
     const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, addr, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
@@ -718,7 +854,7 @@ MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t
     L.wt_rows = 2 * L.n_kb * 128;
     L.P = 2 * m;
     L.rows = 8 * m;
-    L.k_occ_pad = (n_occ + 63) / 64 * 64;  // whole 64-orbital blocks: each staged row segment is one 128 B line
+    L.k_occ_pad = (n_occ + 63) / 64 * 64;  // whole 64-orbital blocks: the spinor tiles write 512 B row segments
     L.k_vir_pad = (n_vir + 63) / 64 * 64;
     L.n_tau = n_tau;
     size_t off = align256(offset);
@@ -804,14 +940,14 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
             (rc = encode(plan.maps_spinor[7], ws + L.WTS_lo, 2, wsd, ss_, err)))
             return rc;
     }
-    // Contraction: planes [4 n_tau][rows][k_pad] as a 3-D tensor (orbital, row, 4 tau + plane).
+    // Contraction: operand rows [n_tau][rows][4 k_pad] as a 3-D tensor (chunk x plane x orbital, row, tau).
     {
-        const cuuint64_t dO[3] = {(cuuint64_t)s.n_occ, (cuuint64_t)L.rows, (cuuint64_t)4 * L.n_tau};
-        const cuuint64_t sO[2] = {(cuuint64_t)L.k_occ_pad * 2, (cuuint64_t)L.rows * L.k_occ_pad * 2};
-        const cuuint64_t dV[3] = {(cuuint64_t)s.n_vir, (cuuint64_t)L.rows, (cuuint64_t)4 * L.n_tau};
-        const cuuint64_t sV[2] = {(cuuint64_t)L.k_vir_pad * 2, (cuuint64_t)L.rows * L.k_vir_pad * 2};
-        if ((rc = encode(plan.maps_pairs[0], ws + L.occ_planes, 3, dO, sO, err)) ||
-            (rc = encode(plan.maps_pairs[1], ws + L.vir_planes, 3, dV, sV, err)))
+        const cuuint64_t dO[3] = {(cuuint64_t)4 * L.k_occ_pad, (cuuint64_t)L.rows, (cuuint64_t)L.n_tau};
+        const cuuint64_t sO[2] = {(cuuint64_t)L.k_occ_pad * 8, (cuuint64_t)L.rows * L.k_occ_pad * 8};
+        const cuuint64_t dV[3] = {(cuuint64_t)4 * L.k_vir_pad, (cuuint64_t)L.rows, (cuuint64_t)L.n_tau};
+        const cuuint64_t sV[2] = {(cuuint64_t)L.k_vir_pad * 8, (cuuint64_t)L.rows * L.k_vir_pad * 8};
+        if ((rc = encode(plan.maps_pairs[0], ws + L.occ_planes, 3, dO, sO, err, 4 * PR_BK, CU_TENSOR_MAP_SWIZZLE_128B)) ||
+            (rc = encode(plan.maps_pairs[1], ws + L.vir_planes, 3, dV, sV, err, 4 * PR_BK, CU_TENSOR_MAP_SWIZZLE_128B)))
             return rc;
     }
     if (cudaFuncSetAttribute(spinor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM) !=

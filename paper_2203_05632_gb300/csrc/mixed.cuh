@@ -15,7 +15,7 @@ struct MixedLayout {
     int P, rows, k_occ_pad, k_vir_pad, n_tau;
     size_t BL_hi, BL_lo, BS_hi, BS_lo;      // basis values / gradients, BF16 hi/lo: [P][nl_pad], [P][nl3_pad]
     size_t WTL_hi, WTL_lo, WTS_hi, WTS_lo;  // transposed spinor coefficients, BF16 hi/lo: [wt_rows][nl(3)_pad]
-    size_t occ_planes, vir_planes;          // X planes of all times: [n_tau][4][rows][k_pad]
+    size_t occ_planes, vir_planes;          // split X of all times: [n_tau][rows][k_pad / 16][4 planes][16]
     size_t flag;                            // time-out flag word
     size_t end;
 };

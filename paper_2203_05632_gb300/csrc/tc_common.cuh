@@ -67,6 +67,15 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abor
     }
 }
 
+// mbar_wait with an inlined first test: a hot issue loop pays for the call
+// (and the timer reads) only when the phase is not complete yet.
+__device__ __forceinline__ bool mbar_wait_fast(uint64_t *bar, uint32_t parity, int *abort_flag, int code,
+                                               unsigned long long timeout_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait(bar, parity, abort_flag, code, timeout_ns);
+}
+
 // Waits (bounded, no flag) until the phase completes; used to drain copies before exit.
 __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, unsigned long long timeout_ns)
 {
