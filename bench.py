@@ -37,6 +37,7 @@ WORKLOAD = ("medium: 6 centres (4 x Z=50, 2 x Z=17), n_L=300 (+600 small), 80 oc
             "m=1024 walker pairs, 4 tau per step")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 CUDA-core FP64 (no FP64 tensor path on this part)
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 
 
 def flops_per_sample(n_occ, n_vir):
@@ -163,14 +164,23 @@ def time_steps(ctx, torch, steps, seed, flush):
     return total
 
 
+def issued_per_algorithmic(n_occ, n_vir, products):
+    """Tensor flops the contraction issues per algorithmic flop: every 128 x 128
+    tile computes all four electron blocks of G- (the trace form needs two) and
+    G+ (it needs all four), `products` split products per real product."""
+    issued = products * 8 * 64 * (n_occ + n_vir)
+    return issued / flops_per_sample(n_occ, n_vir)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "tf32", "fp64"], default="mixed")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form beside the mixed run")
+    ap.add_argument("--tf32-steps", type=int, default=200, help="timed steps of the TF32 form beside the mixed run")
     ap.add_argument("--stat-steps", type=int, default=10000, help="steps of the run that estimates sigma for time-to-0.1%%")
     ap.add_argument("--cpu-sample-m", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -199,7 +209,7 @@ def main():
 
     system = synthetic.make_system("medium")
     peaks, peak_kind = load_peaks()
-    prec = pkg.MCMP2_MIXED if args.precision == "mixed" else pkg.MCMP2_FP64
+    prec = {"mixed": pkg.MCMP2_MIXED, "tf32": pkg.MCMP2_TF32, "fp64": pkg.MCMP2_FP64}[args.precision]
     seed = 5632 + rank
     m_run = args.m
     samples_per_step = m_run * (m_run - 1) // 2 * N_TAU
@@ -272,7 +282,7 @@ def main():
         sctx.close()
 
     fp64 = None
-    if prec == pkg.MCMP2_MIXED and args.fp64_steps > 0:
+    if prec != pkg.MCMP2_FP64 and args.fp64_steps > 0:
         fctx = make_ctx(pkg.MCMP2_FP64)
         fctx.run_steps(1, seed)
         fctx.profile(1)
@@ -285,11 +295,40 @@ def main():
                 "achieved_tflops": flop_unit * samples_per_step / (f_pair / 1e3) / 1e12}
         fctx.close()
 
+    tf32 = None
+    if prec == pkg.MCMP2_MIXED and args.tf32_steps > 0:
+        tctx = make_ctx(pkg.MCMP2_TF32)
+        tctx.run_steps(3, seed)
+        tctx.profile(1)
+        t_ms = time_steps(tctx, torch, args.tf32_steps, seed, flush)
+        tp = tctx.profile(0)
+        tctx.profile(2)
+        t_pair = tp["pair_ms"] / max(1, tp["pair_launches"])
+        t_ach = flop_unit * samples_per_step / (t_pair / 1e3) / 1e12
+        t_peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]) * TF32_OVER_BF16
+        tf32 = {"value": args.tf32_steps * samples_per_step / (t_ms / 1e3), "ms_per_step": t_ms / args.tf32_steps,
+                "pair_kernel_ms": t_pair, "achieved_tflops": t_ach,
+                "roofline_frac": t_ach / t_peak, "peak_tflops": t_peak,
+                "issued_frac": t_ach * issued_per_algorithmic(system.n_occ, system.n_vir, 1) / t_peak,
+                "peak_kind": f"{peak_kind} bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)"}
+        tctx.close()
+
     if prec == pkg.MCMP2_MIXED:
         peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+        issued = achieved * issued_per_algorithmic(system.n_occ, system.n_vir, 3)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "peak_kind": f"{peak_kind} bf16 sustained"}
+                "peak_kind": f"{peak_kind} bf16 sustained",
+                "issued": {"tflops": issued, "frac": issued / peak,
+                           "note": "BF16 tensor work actually issued: 3 split products, full 128 x 128 tiles"}}
+    elif prec == pkg.MCMP2_TF32:
+        peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]) * TF32_OVER_BF16
+        issued = achieved * issued_per_algorithmic(system.n_occ, system.n_vir, 1)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": f"{peak_kind} bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)",
+                "issued": {"tflops": issued, "frac": issued / peak,
+                           "note": "TF32 tensor work actually issued: full 128 x 128 tiles"}}
     else:
         peak = FP64_NOMINAL_TFLOPS
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -306,7 +345,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3" if prec == pkg.MCMP2_MIXED else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {pkg.MCMP2_MIXED: "bf16x3", pkg.MCMP2_TF32: "tf32"}.get(prec, "f64"),
+            "data": "synthetic",
             "config": {"workload": WORKLOAD if m_run == M else WORKLOAD.replace("m=1024", f"m={m_run}"),
                        "precision": args.precision, "l2": "flushed between timed steps",
                        "parallelism": f"{world} independent replicas"},
@@ -317,6 +357,7 @@ def main():
             "roofline": roof,
             "time_to_0.1pct": stat,
             "fp64_form": fp64,
+            "tf32_form": tf32,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

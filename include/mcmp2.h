@@ -62,6 +62,9 @@ extern "C" {
 /* Arithmetic of the propagator and spinor contractions. */
 #define MCMP2_FP64 0   /* complex128 throughout (CUDA-core DFMA) */
 #define MCMP2_MIXED 1  /* split-BF16 x3 tensor-core products, FP32 accumulate; FP64 sampling and sums */
+#define MCMP2_TF32 2   /* as MCMP2_MIXED, but the propagators are single TF32 tensor-core products of
+                        * operands rounded to nearest TF32 (10-bit significand): 2/3 of the MMAs,
+                        * relative error per operand <= 2^-11, unbiased */
 
 /* Sampling constants (Sec. III leaves them open; see the library design notes). */
 #define MCMP2_DELTA0 0.6        /* initial Metropolis displacement (bohr) */
@@ -106,8 +109,8 @@ typedef struct {
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
  * (a cudaStream_t; NULL for the legacy default stream) in `precision`
- * (MCMP2_FP64 or MCMP2_MIXED).  Fails with MCMP2_EUNSUPPORTED on devices
- * other than compute capability 10.3. */
+ * (MCMP2_FP64, MCMP2_MIXED or MCMP2_TF32).  Fails with MCMP2_EUNSUPPORTED on
+ * devices other than compute capability 10.3. */
 int mcmp2_create(mcmp2_ctx **ctx, int device, void *cuda_stream, int precision);
 
 /* Release the context (not the caller's workspace).  NULL is ignored. */

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "mcmp2.h")
 MCMP2_OK = 0
 MCMP2_FP64 = 0
 MCMP2_MIXED = 1
+MCMP2_TF32 = 2
 STATUS = {-1: "EINVAL", -2: "ENOTLOADED", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT", -6: "ENOSPACE",
           -7: "EUNSUPPORTED"}
 

@@ -42,6 +42,14 @@ constexpr int TILE_BYTES = 128 * BK * 2;                  // one 128 x 32 BF16 o
 
 __device__ __forceinline__ int n_chunks(int k) { return (k + BK - 1) / BK; }
 
+// FP32 rounded to the nearest TF32 value (ties away from zero), low 13 bits zero.
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -115,10 +123,11 @@ struct SpinorMaps {
 
 struct SpinorArgs {
     const float *scale;   // [n_tau][n_orb]
-    __nv_bfloat16 *occ;   // [n_tau][rows][k_occ_pad / 16][4 planes][16]
-    __nv_bfloat16 *vir;   // [n_tau][rows][k_vir_pad / 16][4 planes][16]
+    __nv_bfloat16 *occ;   // [n_tau][rows][k_occ_pad / 16][128 B]
+    __nv_bfloat16 *vir;   // [n_tau][rows][k_vir_pad / 16][128 B]
     int *abort_flag;
     int P, nl, n_mt, n_kb, n_kb_occ, n_occ, n_vir, n_orb, n_tau, rows, k_occ_pad, k_vir_pad;
+    int tf32;  // chunk = 16 re (TF32) + 16 im (TF32) instead of re_hi, re_lo, im_hi, im_lo (BF16)
 };
 
 __device__ __forceinline__ void sp_tile(int tile, int n_kb, int &mt, int &c4, int &kb)
@@ -253,8 +262,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         // Epilogue: each lane owns one position row of the tile.  For every time
         // the warp stages its 32 rows x 64 orbitals in shared memory in the
         // contraction's operand order (per 16-orbital chunk: re_hi, re_lo, im_hi,
-        // im_lo, 32 B each), then writes each row's 512 contiguous bytes with one
-        // 16-byte store per lane.
+        // im_lo, 32 B each; or re, im as TF32, 64 B each), then writes each row's
+        // 512 contiguous bytes with one 16-byte store per lane.
         const int ew = warp - 2;
         const int quarter = warp & 3;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -289,28 +298,43 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                     tmem_ld<16>(lane_addr + 128u * buf + 16u * j, re);
                     tmem_ld<16>(lane_addr + 128u * buf + 64u + 16u * j, im);
                     tmem_wait_ld();
-                    uint32_t rh[8], rl[8], ih[8], il[8];
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const float s0 = st_[16 * j + i], s1 = st_[16 * j + i + 1];
-                        const float xr0 = re[i] * s0, xr1 = re[i + 1] * s1;
-                        const float xi0 = im[i] * s0, xi1 = im[i + 1] * s1;
-                        const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
-                        const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
-                        rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
-                        ih[i / 2] = *reinterpret_cast<const uint32_t *>(&hi);
-                        rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
-                        il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
-                    }
                     uint4 *d = reinterpret_cast<uint4 *>(wstage + lane * SP_ROW_BYTES + 128 * j);
-                    d[0] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                    d[1] = make_uint4(rh[4], rh[5], rh[6], rh[7]);
-                    d[2] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                    d[3] = make_uint4(rl[4], rl[5], rl[6], rl[7]);
-                    d[4] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                    d[5] = make_uint4(ih[4], ih[5], ih[6], ih[7]);
-                    d[6] = make_uint4(il[0], il[1], il[2], il[3]);
-                    d[7] = make_uint4(il[4], il[5], il[6], il[7]);
+                    if (args.tf32) {
+                        uint32_t rt[16], it[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float sc = st_[16 * j + i];
+                            rt[i] = to_tf32(re[i] * sc);
+                            it[i] = to_tf32(im[i] * sc);
+                        }
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            d[v] = make_uint4(rt[4 * v], rt[4 * v + 1], rt[4 * v + 2], rt[4 * v + 3]);
+                            d[4 + v] = make_uint4(it[4 * v], it[4 * v + 1], it[4 * v + 2], it[4 * v + 3]);
+                        }
+                    } else {
+                        uint32_t rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            const float s0 = st_[16 * j + i], s1 = st_[16 * j + i + 1];
+                            const float xr0 = re[i] * s0, xr1 = re[i + 1] * s1;
+                            const float xi0 = im[i] * s0, xi1 = im[i + 1] * s1;
+                            const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
+                            const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
+                            rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
+                            ih[i / 2] = *reinterpret_cast<const uint32_t *>(&hi);
+                            rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
+                            il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
+                        }
+                        d[0] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                        d[1] = make_uint4(rh[4], rh[5], rh[6], rh[7]);
+                        d[2] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                        d[3] = make_uint4(rl[4], rl[5], rl[6], rl[7]);
+                        d[4] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                        d[5] = make_uint4(ih[4], ih[5], ih[6], ih[7]);
+                        d[6] = make_uint4(il[0], il[1], il[2], il[3]);
+                        d[7] = make_uint4(il[4], il[5], il[6], il[7]);
+                    }
                 }
                 __syncwarp();
 #pragma unroll 4
@@ -346,6 +370,9 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
 // for each 16-orbital chunk the four split planes re_hi, re_lo, im_hi, im_lo
 // side by side (128 B), so one 128-byte-swizzled TMA box of 128 rows brings
 // all four planes of a chunk and the MMA selects a plane by a 32-byte offset.
+// In the TF32 form the 128 B are re and im of the chunk as TF32 (64 B each);
+// the same offsets then select (re, K 0-7), (re, K 8-15), (im, K 0-7), (im,
+// K 8-15), and a chunk takes 8 MMAs (K = 8) instead of 12.
 //
 // Work item = (tile of 16 x 16 walker pairs, time).  Per item the tensor
 // cores accumulate G- (K = n_occ) and then G+ (K = n_vir) as 128 x 128
@@ -451,6 +478,7 @@ __device__ __forceinline__ void group_sync(int g)
         bar_sync<2, 32 * PR_GROUP_WARPS>();
 }
 
+template <bool TF32>
 __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid_constant__ PairMaps maps,
                                                                     const PairArgs args)
 {
@@ -543,7 +571,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             uint32_t phase = 0;
             uint32_t use[PR_GROUPS] = {0, 0};  // parity of each group's uses so far
             bool ok = true;
-            const uint32_t id_pos = idesc_bf16(128, false), id_neg = idesc_bf16(128, true);
+            const uint32_t id_pos = TF32 ? idesc_tf32(128, false) : idesc_bf16(128, false);
+            const uint32_t id_neg = TF32 ? idesc_tf32(128, true) : idesc_bf16(128, true);
             // Descriptors of stage 0; stage s adds s * PR_STAGE_BYTES to the start-address
             // field (address >> 4 in the low 14 bits, no carry for addresses below 256 KB).
             // Keeping this loop short matters: the tensor pipe drains while it runs.
@@ -584,18 +613,30 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                     // Re G += Xr Yr^T + Xi Yi^T and Im G += Xi Yr^T - Xr Yi^T, alternating
                     // between the two accumulators.  (Straight-line code: the issue loop
                     // must stay short, the tensor pipe drains while it runs.)
-                    umma(d_re, arh, brh, id_pos, acc);
-                    umma(d_im, aih, brh, id_pos, acc);
-                    umma(d_re, arh, brl, id_pos, 1u);
-                    umma(d_im, aih, brl, id_pos, 1u);
-                    umma(d_re, arl, brh, id_pos, 1u);
-                    umma(d_im, ail, brh, id_pos, 1u);
-                    umma(d_re, aih, bih, id_pos, 1u);
-                    umma(d_im, arh, bih, id_neg, 1u);
-                    umma(d_re, aih, bil, id_pos, 1u);
-                    umma(d_im, arh, bil, id_neg, 1u);
-                    umma(d_re, ail, bih, id_pos, 1u);
-                    umma(d_im, arl, bih, id_neg, 1u);
+                    if constexpr (TF32) {
+                        // descriptors at +0, +32, +64, +96: re K 0-7, re K 8-15, im K 0-7, im K 8-15
+                        umma_tf32(d_re, arh, brh, id_pos, acc);
+                        umma_tf32(d_im, aih, brh, id_pos, acc);
+                        umma_tf32(d_re, aih, bih, id_pos, 1u);
+                        umma_tf32(d_im, arh, bih, id_neg, 1u);
+                        umma_tf32(d_re, arl, brl, id_pos, 1u);
+                        umma_tf32(d_im, ail, brl, id_pos, 1u);
+                        umma_tf32(d_re, ail, bil, id_pos, 1u);
+                        umma_tf32(d_im, arl, bil, id_neg, 1u);
+                    } else {
+                        umma(d_re, arh, brh, id_pos, acc);
+                        umma(d_im, aih, brh, id_pos, acc);
+                        umma(d_re, arh, brl, id_pos, 1u);
+                        umma(d_im, aih, brl, id_pos, 1u);
+                        umma(d_re, arl, brh, id_pos, 1u);
+                        umma(d_im, ail, brh, id_pos, 1u);
+                        umma(d_re, aih, bih, id_pos, 1u);
+                        umma(d_im, arh, bih, id_neg, 1u);
+                        umma(d_re, aih, bil, id_pos, 1u);
+                        umma(d_im, arh, bil, id_neg, 1u);
+                        umma(d_re, ail, bih, id_pos, 1u);
+                        umma(d_im, arl, bih, id_neg, 1u);
+                    }
                     umma_commit(&empty[stage]);
                     if (++stage == PR_STAGES) {
                         stage = 0;
@@ -952,7 +993,9 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
     }
     if (cudaFuncSetAttribute(spinor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(pairs_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
+        cudaFuncSetAttribute(pairs_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
             cudaSuccess) {
         err = "cannot reserve shared memory for the tensor-core kernels";
         return MCMP2_ECUDA;
@@ -983,7 +1026,7 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     std::memcpy(&smaps, plan.maps_spinor, sizeof(smaps));
     const int n_mt = (L.P + 127) / 128;
     SpinorArgs sa{scale, bf(L.occ_planes), bf(L.vir_planes), flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ,
-                  s.n_occ, s.n_vir, s.n_orb, s.n_tau, L.rows, L.k_occ_pad, L.k_vir_pad};
+                  s.n_occ, s.n_vir, s.n_orb, s.n_tau, L.rows, L.k_occ_pad, L.k_vir_pad, plan.tf32 ? 1 : 0};
     const int sp_tiles = n_mt * 4 * L.n_kb;
     spinor_mixed_kernel<<<sp_tiles < sms ? sp_tiles : sms, SP_THREADS, SP_SMEM, st>>>(smaps, sa);
 
@@ -1000,7 +1043,10 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     }
     const int items = n_tiles * s.n_tau;
     if (ev) record_event(ev[0], st);
-    pairs_mixed_kernel<<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+    if (plan.tf32)
+        pairs_mixed_kernel<true><<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+    else
+        pairs_mixed_kernel<false><<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
     if (ev) record_event(ev[1], st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -198,7 +198,7 @@ int mcmp2_create(mcmp2_ctx **out, int device, void *cuda_stream, int precision)
 {
     if (!out) return MCMP2_EINVAL;
     *out = nullptr;
-    if (precision != MCMP2_FP64 && precision != MCMP2_MIXED) return MCMP2_EINVAL;
+    if (precision != MCMP2_FP64 && precision != MCMP2_MIXED && precision != MCMP2_TF32) return MCMP2_EINVAL;
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return MCMP2_EUNSUPPORTED;
     cudaDeviceProp prop;
@@ -237,7 +237,8 @@ const char *mcmp2_last_error(const mcmp2_ctx *ctx) { return ctx ? ctx->err.c_str
 
 int mcmp2_workspace_bytes(const mcmp2_dims *dims, int precision, size_t *bytes)
 {
-    if (!dims_valid(dims) || !bytes || (precision != MCMP2_FP64 && precision != MCMP2_MIXED))
+    if (!dims_valid(dims) || !bytes ||
+        (precision != MCMP2_FP64 && precision != MCMP2_MIXED && precision != MCMP2_TF32))
         return MCMP2_EINVAL;
     *bytes = make_layout(*dims, precision).total;
     return MCMP2_OK;
@@ -438,7 +439,8 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     ctx->drop_graph();  // kernel arguments captured by value (energies, lambda) change with the system
     if (ctx->precision == MCMP2_FP64) CK(prepare_f64(), "configure FP64 kernels");
     ctx->walkers = false;
-    if (ctx->precision == MCMP2_MIXED) {
+    if (ctx->precision != MCMP2_FP64) {
+        ctx->mixed.tf32 = ctx->precision == MCMP2_TF32;
         const int rc = mixed_prepare(ctx->mixed, S, L.mixed, ctx->ws, WL.data(), WS.data(), st, ctx->err);
         if (rc != MCMP2_OK) {
             ctx->loaded = false;
@@ -476,7 +478,7 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         CK(launch_pair_weights(S, r, a, st), "pair weights");
         ctx->launches += 1;
     }
-    float *scale_f = ctx->precision == MCMP2_MIXED ? ctx->at<float>(L.scale_f) : nullptr;
+    float *scale_f = ctx->precision != MCMP2_FP64 ? ctx->at<float>(L.scale_f) : nullptr;
     CK(launch_times(S, step, seed, tau_given, tau, scale, scale_f, st), "imaginary times");
     ctx->launches += 1;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -509,7 +511,7 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
     }
     CK(launch_reduce(S, partials, L.n_tiles, out_slot, ctx->at<Stats>(L.stats), update, advance ? step : nullptr,
                      ctx->at<ReduceScratch>(L.red), st,
-                     ctx->precision == MCMP2_MIXED ? ctx->at<int>(L.mixed.flag) : nullptr),
+                     ctx->precision != MCMP2_FP64 ? ctx->at<int>(L.mixed.flag) : nullptr),
        "step reduction");
     ctx->launches += 1;
     return MCMP2_OK;
@@ -585,7 +587,7 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
     // One step is captured once into a CUDA graph (its kernels read the step
     // counter from device memory, so the graph is the same for every step)
     // and replayed n times on the caller's stream.
-    if (ctx->precision == MCMP2_MIXED && ctx->mixed.withhold_once_ns && n > 0) {
+    if (ctx->precision != MCMP2_FP64 && ctx->mixed.withhold_once_ns && n > 0) {
         // A pending test stall applies to one directly issued step.
         CK(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta, &stats->accepted,
                              ctx->at<double>(L.a), st),
@@ -651,7 +653,7 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
         if (!std::isfinite(h.all_sum) || !std::isfinite(h.mean) || !std::isfinite(h.m2))
             return ctx->fail(MCMP2_ENONFINITE, "a step estimate is not finite");
     }
-    if (ctx->precision == MCMP2_MIXED && out) {
+    if (ctx->precision != MCMP2_FP64 && out) {
         const int rc = mixed_check_flag(ctx->L.mixed, ctx->ws, st, ctx->err);
         if (rc) return rc;
     }
@@ -686,7 +688,7 @@ int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const doub
         CK(cudaMemcpyAsync(out + s0, slots, sizeof(double) * len, cudaMemcpyDeviceToHost, st), "copy results");
         CK(cudaStreamSynchronize(st), "replay sync");
     }
-    if (ctx->precision == MCMP2_MIXED) {
+    if (ctx->precision != MCMP2_FP64) {
         const int rc = mixed_check_flag(ctx->L.mixed, ctx->ws, st, ctx->err);
         if (rc) return rc;
     }
@@ -857,7 +859,7 @@ int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out)
 int mcmp2_test_stall_next(mcmp2_ctx *ctx, double wait_limit_s)
 {
     if (!ctx) return MCMP2_EINVAL;
-    if (ctx->precision != MCMP2_MIXED) return ctx->fail(MCMP2_EUNSUPPORTED, "the hook applies to the mixed form");
+    if (ctx->precision == MCMP2_FP64) return ctx->fail(MCMP2_EUNSUPPORTED, "the hook applies to the tensor-core forms");
     if (!(wait_limit_s > 0.0) || wait_limit_s > 10.0) return ctx->fail(MCMP2_EINVAL, "wait limit must be in (0, 10] s");
     ctx->mixed.withhold_once_ns = (unsigned long long)(wait_limit_s * 1e9);
     ctx->drop_graph();  // the next step is issued directly, not replayed

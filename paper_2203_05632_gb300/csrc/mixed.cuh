@@ -15,7 +15,7 @@ struct MixedLayout {
     int P, rows, k_occ_pad, k_vir_pad, n_tau;
     size_t BL_hi, BL_lo, BS_hi, BS_lo;      // basis values / gradients, BF16 hi/lo: [P][nl_pad], [P][nl3_pad]
     size_t WTL_hi, WTL_lo, WTS_hi, WTS_lo;  // transposed spinor coefficients, BF16 hi/lo: [wt_rows][nl(3)_pad]
-    size_t occ_planes, vir_planes;          // split X of all times: [n_tau][rows][k_pad / 16][4 planes][16]
+    size_t occ_planes, vir_planes;          // X of all times: [n_tau][rows][k_pad / 16][128 B] (4 BF16 or 2 TF32 planes of 16)
     size_t flag;                            // time-out flag word
     size_t end;
 };
@@ -23,6 +23,7 @@ struct MixedLayout {
 // Host-side state: tensor maps (8 for spinor formation, 2 for the contraction).
 struct MixedPlan {
     bool ready = false;
+    bool tf32 = false;  // propagator operands as TF32 (re, im) instead of split BF16 (re hi/lo, im hi/lo)
     unsigned long long withhold_once_ns = 0;  // test hook for the bounded-wait path (see mcmp2_test_stall_next)
     alignas(64) unsigned char maps_spinor[8][128];
     alignas(64) unsigned char maps_pairs[2][128];

@@ -50,16 +50,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // Bounded wait on a barrier phase.  Returns false (after recording `code` in
 // the abort flag) when timeout_ns elapse, or at once if another role has
-// already set the flag.
+// already set the flag.  The clock is first read after 64 unsuccessful tests
+// (and then every 64): a %globaltimer read stalls the issuing thread for a
+// few hundred cycles, which empties the tensor pipe's queue when the thread
+// is the MMA issuer, so short waits must not pay for it.
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort_flag, int code,
                                        unsigned long long timeout_ns)
 {
-    const unsigned long long t0 = globaltimer();
-    for (uint32_t i = 0;; ++i) {
+    unsigned long long t0 = 0;
+    bool timing = false;
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 63) {
+        if ((i & 63) == 0) {
             if (*(volatile int *)abort_flag) return false;
-            if (globaltimer() - t0 > timeout_ns) {
+            const unsigned long long now = globaltimer();
+            if (!timing) {
+                t0 = now;
+                timing = true;
+            } else if (now - t0 > timeout_ns) {
                 atomicCAS(abort_flag, 0, code);
                 return false;
             }
@@ -125,6 +133,24 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int n, bool negate_a)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((negate_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)(128 >> 4) << 24);
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n, bool negate_a)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
+// D (+)= A B^T with TF32 operands (K = 8 per instruction).
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
