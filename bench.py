@@ -38,6 +38,10 @@ WORKLOAD = ("medium: 6 centres (4 x Z=50, 2 x Z=17), n_L=300 (+600 small), 80 oc
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 CUDA-core FP64 (no FP64 tensor path on this part)
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
+# DRAM bytes (read + write) of one contraction launch at m = 1024, 4 tau, from
+# the ncu captures summarised in profiles/pairs_mixed_{bf16x3,tf32}_medium_m1024.md
+# (the kernels as they stand); None for other sizes.
+PAIRS_TRAFFIC_BYTES = {"mixed": 138.1e6, "tf32": 138.3e6}
 
 
 def flops_per_sample(n_occ, n_vir):
@@ -317,7 +321,7 @@ def main():
         peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
         issued = achieved * issued_per_algorithmic(system.n_occ, system.n_vir, 3)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES["mixed"] if m_run == M else None,
                 "peak_kind": f"{peak_kind} bf16 sustained",
                 "issued": {"tflops": issued, "frac": issued / peak,
                            "note": "BF16 tensor work actually issued: 3 split products, full 128 x 128 tiles"}}
@@ -325,7 +329,7 @@ def main():
         peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]) * TF32_OVER_BF16
         issued = achieved * issued_per_algorithmic(system.n_occ, system.n_vir, 1)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES["tf32"] if m_run == M else None,
                 "peak_kind": f"{peak_kind} bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)",
                 "issued": {"tflops": issued, "frac": issued / peak,
                            "note": "TF32 tensor work actually issued: full 128 x 128 tiles"}}
