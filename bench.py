@@ -107,11 +107,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_oracle_rate(system, m_sample, n_tau, seed=1, steps=1):
+def cpu_oracle_rate(system, m_sample, n_tau, seed=1, steps=1, n_threads=None):
     """Pair-pair samples/s of the oracle on this host's cores (bounded sample)."""
     import oracle
     import synthetic
-    orc = oracle.Oracle(system)
+    orc = oracle.Oracle(system, n_threads=n_threads)
     r = synthetic.walker_positions(system.centres, steps, m_sample, seed=seed)
     tau = synthetic.imaginary_times(orc.lam(), steps, n_tau, seed=seed + 1)
     t0 = time.perf_counter()
@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--tf32-steps", type=int, default=200, help="timed steps of the TF32 form beside the mixed run")
     ap.add_argument("--stat-steps", type=int, default=10000, help="steps of the run that estimates sigma for time-to-0.1%%")
     ap.add_argument("--cpu-sample-m", type=int, default=1024)
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--m", type=int, default=M, help="walker pairs (the workload is m=1024; smaller m only "
                                                      "for sized profiler captures)")
@@ -340,10 +341,13 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, dt, n, cores = cpu_oracle_rate(system, args.cpu_sample_m, N_TAU)
+        rate, dt, n, cores = cpu_oracle_rate(system, args.cpu_sample_m, N_TAU, steps=args.cpu_sample_steps)
+        rate1, dt1, n1, _ = cpu_oracle_rate(system, 128, N_TAU, seed=3, n_threads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"one step of m={args.cpu_sample_m} walker pairs x {N_TAU} tau of the medium system "
-                         f"({n} pair-pair samples, {dt:.1f} s)"}
+               "sample": f"{args.cpu_sample_steps} step(s) of m={args.cpu_sample_m} walker pairs x {N_TAU} tau of the "
+                         f"medium system ({n} pair-pair samples, {dt:.1f} s)",
+               "one_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                            "sample": f"one step of m=128 x {N_TAU} tau ({n1} samples, {dt1:.1f} s)"}}
 
     if rank == 0:
         line = {
