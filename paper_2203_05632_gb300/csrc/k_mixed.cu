@@ -107,15 +107,17 @@ __global__ void basis_split_kernel(DevSystem s, const double *__restrict__ r, __
 // ===========================================================================
 constexpr int SP_STAGES = 4;
 constexpr int SP_STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo
-constexpr int SP_THREADS = 192;                 // TMA warp, MMA warp, 4 epilogue warps
+constexpr int SP_EPI_WARPS = 8;                 // two per tensor-memory lane quarter, one per half tile
+constexpr int SP_THREADS = 64 + 32 * SP_EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
 constexpr int SP_TMEM_COLS = 256;               // two 128-column accumulators
 constexpr int SP_MAX_TAU = 64;                  // scale staging capacity (the API limits n_tau to 64)
-constexpr int SP_ROW_BYTES = 528;               // staged row: 4 chunks x 4 planes x 16 BF16 (512 B) + 16 B pad
+constexpr int SP_ROW_BYTES = 272;               // staged half row: 2 chunks x 128 B + 16 B pad
 constexpr int SP_WARP_STAGE = 32 * SP_ROW_BYTES;  // 32 rows per epilogue warp
 constexpr int SP_BARS_OFF = SP_STAGES * SP_STAGE_BYTES;
 constexpr int SP_SCALE_OFF = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16;
 constexpr int SP_WSTAGE_OFF = SP_SCALE_OFF + SP_MAX_TAU * 64 * 4;
-constexpr int SP_SMEM = SP_WSTAGE_OFF + 4 * SP_WARP_STAGE + 1024;
+constexpr int SP_SMEM = SP_WSTAGE_OFF + SP_EPI_WARPS * SP_WARP_STAGE + 1024;
+static_assert(SP_SMEM <= 232448, "spinor kernel exceeds the shared memory of one CTA");
 
 struct SpinorMaps {
     CUtensorMap m[8];  // 0..3: A_L hi, A_L lo, B_L hi, B_L lo; 4..7: the same for the gradient part
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], SP_EPI_WARPS);
         }
         mbar_init_fence();
     }
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                 const int K = grad ? 3 * args.nl : args.nl;
                 const int wt_row = ((c4 & 1) * args.n_kb + kb) * 128;
                 for (int c = 0; c < n_chunks(K); ++c) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, args.abort_flag, 11, TIMEOUT_NS)) {
+                    if (!mbar_wait_fast(&empty[stage], phase ^ 1u, args.abort_flag, 11, TIMEOUT_NS)) {
                         ok = false;
                         break;
                     }
@@ -214,31 +216,31 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             uint32_t phase = 0, tphase[2] = {0, 0};
             bool ok = true;
             const uint32_t id = idesc_bf16(128, false);
+            // Stage-0 descriptors; a stage or K step adds its byte offset / 16 to the address field.
+            const uint32_t base0 = smem_u32(smem);
+            const uint64_t ah0 = sdesc_sw64(base0 + 0 * TILE_BYTES), al0 = sdesc_sw64(base0 + 1 * TILE_BYTES);
+            const uint64_t bh0 = sdesc_sw64(base0 + 2 * TILE_BYTES), bl0 = sdesc_sw64(base0 + 3 * TILE_BYTES);
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 int mt, c4, kb;
                 sp_tile(tile, args.n_kb, mt, c4, kb);
                 const int K = c4 >= 2 ? 3 * args.nl : args.nl;
-                if (!mbar_wait(&tempty[buf], tphase[buf] ^ 1u, args.abort_flag, 12, TIMEOUT_NS)) {
+                if (!mbar_wait_fast(&tempty[buf], tphase[buf] ^ 1u, args.abort_flag, 12, TIMEOUT_NS)) {
                     ok = false;
                     break;
                 }
                 fence_after();
                 const uint32_t d = tmem + 128u * buf;
                 for (int c = 0; c < n_chunks(K); ++c) {
-                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 13, TIMEOUT_NS)) {
+                    if (!mbar_wait_fast(&full[stage], phase, args.abort_flag, 13, TIMEOUT_NS)) {
                         ok = false;
                         break;
                     }
                     fence_after();
                     const int kvalid = K - c * BK;
                     const int ksteps = kvalid >= BK ? BK / 16 : (kvalid + 15) / 16;
-                    const uint32_t base = smem_u32(smem + stage * SP_STAGE_BYTES);
                     for (int ks = 0; ks < ksteps; ++ks) {
-                        const uint32_t off = ks * 32;
-                        const uint64_t ah = sdesc_sw64(base + 0 * TILE_BYTES + off);
-                        const uint64_t al = sdesc_sw64(base + 1 * TILE_BYTES + off);
-                        const uint64_t bh = sdesc_sw64(base + 2 * TILE_BYTES + off);
-                        const uint64_t bl = sdesc_sw64(base + 3 * TILE_BYTES + off);
+                        const uint64_t so = (uint64_t)((stage * SP_STAGE_BYTES + ks * 32) >> 4);
+                        const uint64_t ah = ah0 + so, al = al0 + so, bh = bh0 + so, bl = bl0 + so;
                         umma(d, ah, bh, id, (c == 0 && ks == 0) ? 0u : 1u);
                         umma(d, ah, bl, id, 1u);
                         umma(d, al, bh, id, 1u);
@@ -259,13 +261,15 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             mbar_drain(&empty[stage], phase, TIMEOUT_NS);
         }
     } else {
-        // Epilogue: each lane owns one position row of the tile.  For every time
-        // the warp stages its 32 rows x 64 orbitals in shared memory in the
+        // Epilogue: each lane owns one position row of the tile; the two warps of a
+        // lane quarter take orbitals 0-31 and 32-63 of the 64-orbital block.  For
+        // every time a warp stages its 32 rows x 32 orbitals in shared memory in the
         // contraction's operand order (per 16-orbital chunk: re_hi, re_lo, im_hi,
-        // im_lo, 32 B each; or re, im as TF32, 64 B each), then writes each row's
-        // 512 contiguous bytes with one 16-byte store per lane.
+        // im_lo, 32 B each; or re, im as TF32, 64 B each), then writes the rows'
+        // 256-byte segments, two rows per store instruction.
         const int ew = warp - 2;
         const int quarter = warp & 3;
+        const int jh = ew >> 2;  // which 32 orbitals of the block
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
         float *sscale = reinterpret_cast<float *>(smem + SP_SCALE_OFF);  // [n_tau][64]
         unsigned char *wstage = smem + SP_WSTAGE_OFF + ew * SP_WARP_STAGE;
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             int mt, c4, kb;
             sp_tile(tile, args.n_kb, mt, c4, kb);
             const bool got = mbar_wait(&tfull[buf], ephase[buf], args.abort_flag, 14, TIMEOUT_NS);
-            if (bar_any<1, 128>(!got)) break;  // also: every epilogue warp is done with the previous scales
+            if (bar_any<1, 32 * SP_EPI_WARPS>(!got)) break;  // also: every epilogue warp is done with the previous scales
             ephase[buf] ^= 1u;
             fence_after();
             const bool occ = kb < args.n_kb_occ;
@@ -285,20 +289,20 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             const int k_end = occ ? args.n_occ : args.n_orb;       // one past the region's last orbital
             __nv_bfloat16 *planes = occ ? args.occ : args.vir;
             const size_t time_elems = (size_t)args.rows * 4 * kpad;  // one time's operand rows
-            for (int i = threadIdx.x - 64; i < 64 * args.n_tau; i += 128) {
+            for (int i = threadIdx.x - 64; i < 64 * args.n_tau; i += 32 * SP_EPI_WARPS) {
                 const int t = i >> 6, k = k_first + (i & 63);
                 sscale[i] = k < k_end ? args.scale[(size_t)t * args.n_orb + k] : 0.f;
             }
-            bar_sync<1, 128>();
+            bar_sync<1, 32 * SP_EPI_WARPS>();
             for (int t = 0; t < args.n_tau; ++t) {
                 const float *st_ = sscale + 64 * t;
 #pragma unroll 1
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 2 * jh; j < 2 * jh + 2; ++j) {
                     float re[16], im[16];
                     tmem_ld<16>(lane_addr + 128u * buf + 16u * j, re);
                     tmem_ld<16>(lane_addr + 128u * buf + 64u + 16u * j, im);
                     tmem_wait_ld();
-                    uint4 *d = reinterpret_cast<uint4 *>(wstage + lane * SP_ROW_BYTES + 128 * j);
+                    uint4 *d = reinterpret_cast<uint4 *>(wstage + lane * SP_ROW_BYTES + 128 * (j - 2 * jh));
                     if (args.tf32) {
                         uint32_t rt[16], it[16];
 #pragma unroll
@@ -337,13 +341,15 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                     }
                 }
                 __syncwarp();
+                const int half = lane >> 4, piece = lane & 15;
 #pragma unroll 4
-                for (int it = 0; it < 32; ++it) {
-                    const int x = mt * 128 + 32 * quarter + it;
+                for (int it = 0; it < 16; ++it) {
+                    const int row = 2 * it + half;
+                    const int x = mt * 128 + 32 * quarter + row;
                     if (x < args.P) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(wstage + it * SP_ROW_BYTES + 16 * lane);
-                        __nv_bfloat16 *dst =
-                            planes + (size_t)t * time_elems + (size_t)(4 * x + c4) * (4 * kpad) + kl * 256 + 8 * lane;
+                        const uint4 v = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * piece);
+                        __nv_bfloat16 *dst = planes + (size_t)t * time_elems + (size_t)(4 * x + c4) * (4 * kpad) +
+                                             kl * 256 + jh * 128 + 8 * piece;
                         *reinterpret_cast<uint4 *>(dst) = v;
                     }
                 }

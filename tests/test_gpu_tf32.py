@@ -34,14 +34,14 @@ def _abs_expansion_sum(orc, system, r_step, tau_step, pairs=None):
     e_h, e_l = eps[:n_occ].max(), eps[n_occ:].min()
     lam = 2.0 * (e_l - e_h)
     ng = orc.Ng()
-    phi = np.empty((m, 2, orc.n_orb, 4), dtype=np.complex128)
-    a = np.empty(m)
-    for p in range(m):
+    if pairs is None:
+        pairs = [(p, q) for p in range(m) for q in range(p + 1, m)]
+    phi = np.zeros((m, 2, orc.n_orb, 4), dtype=np.complex128)
+    a = np.zeros(m)
+    for p in sorted({i for pq in pairs for i in pq}):
         for e in range(2):
             phi[p, e] = orc.spinors_at(r_step[p, e])
         a[p] = ng / (orc.g(r_step[p, 0]) * orc.g(r_step[p, 1]))
-    if pairs is None:
-        pairs = [(p, q) for p in range(m) for q in range(p + 1, m)]
     total = np.zeros(len(tau_step))
     for t, tau in enumerate(tau_step):
         s_occ = np.exp((eps[:n_occ] - e_h) * tau / 2.0)
@@ -143,3 +143,38 @@ def test_tf32_walk_checkpoint_round_trip(tiny_soft):
     b = other.run_steps(90, seed)
     assert a == b
     assert a["steps"] == 210 and a["n_blocks"] == 2 and np.isfinite(a["energy"])
+
+
+def _tile_pairs(bp, bq, tp, m):
+    out = []
+    for i in range(tp):
+        for j in range(tp):
+            p, q = bp * tp + i, bq * tp + j
+            if p < m and q < m and (bp < bq or i < j):
+                out.append((p, q))
+    return out
+
+
+def test_tf32_full_size_sampled_tiles_match_oracle():
+    """The bench configuration (m = 1024, 4 times): sampled 16 x 16 tiles against the oracle's
+    per-pair values, each tile's partial sum within 8u times the tile's absolute expansion."""
+    medium = synthetic.make_system("medium")
+    orc = oracle.Oracle(medium)
+    m, n_tau = 1024, 4
+    r = synthetic.walker_positions(medium.centres, 1, m, seed=51)
+    tau = synthetic.imaginary_times(orc.lam(), 1, n_tau, seed=52)
+    ctx = pkg.Context(medium, m, n_tau, pkg.MCMP2_TF32)
+    step = ctx.eval_fixed(r, tau)[0]
+    partials, tp = ctx.debug_partials()
+    assert tp == 16
+    nb = (m + tp - 1) // tp
+    assert step == pytest.approx(partials.sum() / (m * (m - 1) / 2) / n_tau, rel=1e-12)
+    for bp, bq in [(0, 0), (7, 40), (nb - 1, nb - 1)]:
+        pairs = _tile_pairs(bp, bq, tp, m)
+        ps = np.array([p for p, _ in pairs])
+        qs = np.array([q for _, q in pairs])
+        want = orc.eval_pairs(r[0], tau[0], ps, qs).sum(axis=0)
+        bound = 8.0 * U_TF32 * _abs_expansion_sum(orc, medium, r[0][: max(ps.max(), qs.max()) + 1], tau[0], pairs)
+        k = sum(nb - b for b in range(bp)) + (bq - bp)
+        got = partials[:, k]
+        assert np.all(np.abs(got - want) <= bound), (bp, bq, got, want, bound)
