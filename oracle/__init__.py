@@ -66,6 +66,7 @@ class OrSystem(ctypes.Structure):
         ("n_vir", ctypes.c_int),
         ("C", ctypes.c_void_p),
         ("eps", ctypes.c_void_p),
+        ("interaction", ctypes.c_int),
     ]
 
 
@@ -122,8 +123,15 @@ BLOCK_SIZE = 100      # Flyvbjerg-Petersen block size N_b (Sec. IV)
 class Oracle:
     """The oracle bound to one system (a ``synthetic.System``)."""
 
-    def __init__(self, system, n_threads: int | None = None):
+    COULOMB, GAUNT, BREIT = 0, 1, 2
+
+    def __init__(self, system, n_threads: int | None = None, interaction: int = 0):
+        """interaction: 0 Coulomb (the paper's runs), 1 Coulomb + Gaunt, 2 Coulomb + Gaunt + gauge
+        (the full Breit operator of Sec. II)."""
+        if interaction not in (0, 1, 2):
+            raise ValueError("interaction must be 0, 1 or 2")
         self.system = system
+        self.interaction = interaction
         self._keep = dict(
             centres=_f64(system.centres), weight=_f64(system.weight),
             shell_centre=np.ascontiguousarray(system.shell_centre, dtype=np.int32),
@@ -134,7 +142,8 @@ class Oracle:
         self._sys = OrSystem(len(k["centres"]), _ptr(k["centres"]).value, _ptr(k["weight"]).value,
                              len(k["shell_l"]), _ptr(k["shell_centre"]).value, _ptr(k["shell_l"]).value,
                              _ptr(k["shell_alpha"]).value, _ptr(k["shell_coef"]).value,
-                             int(system.n_occ), int(system.n_vir), _ptr(k["C"]).value, _ptr(k["eps"]).value)
+                             int(system.n_occ), int(system.n_vir), _ptr(k["C"]).value, _ptr(k["eps"]).value,
+                             int(interaction))
         self.L = lib()
         self.n_threads = n_threads or self.L.or_max_threads()
 

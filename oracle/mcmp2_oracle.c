@@ -56,6 +56,7 @@ typedef struct {
     int n_occ, n_vir;
     const double *C;          /* complex interleaved, [4 n_L][n_orb] row-major */
     const double *eps;        /* [n_orb], occupied first */
+    int interaction;          /* 0: Coulomb 1/r12; 1: + Gaunt; 2: + Gaunt + gauge (full Breit) */
 } or_system;
 
 /* ---------------------------------------------------------------------- */
@@ -249,11 +250,90 @@ static void matmul4(cplx A[4][4], cplx B[4][4], cplx out[4][4])
 
 static cplx trace4(cplx A[4][4]) { return A[0][0] + A[1][1] + A[2][2] + A[3][3]; }
 
-/* f(r1,r2,r3,r4,tau) * r12 * r34 at one sample, the two integrands of the
- * trace-form Eq. MCMP2:  -1/2 { tr[G-31 G+13] tr[G-42 G+24] - tr[G-31 G+14 G-42 G+23] }. */
-static cplx integrand(const or_system *s, const cplx *p1, const cplx *p2, const cplx *p3,
-                      const cplx *p4, double tau)
+/* The interaction between electrons a and b (Sec. II, operator g_ij):
+ *   g(a,b) = 1/r_ab - alpha(a).alpha(b) / (2 r_ab) - (alpha(a).r_ab)(alpha(b).r_ab) / (2 r_ab^3)
+ *          = (1/r_ab) sum_A c_A O_A(a) O_A(b),
+ * with O_0 = 1 (c = 1), O_k = alpha_k (k = x, y, z; c = -1/2) for the Gaunt term and
+ * O_n = alpha.n, n = r_ab / r_ab (c = -1/2) for the gauge term.  alpha_k has sigma_k in its
+ * off-diagonal 2x2 blocks (components L-alpha, L-beta, S-alpha, S-beta).  Returns the count. */
+static int interaction_terms(const or_system *s, const double *ra, const double *rb, cplx O[5][4][4],
+                             double c[5])
 {
+    static const cplx sig[3][2][2] = {{{0, 1}, {1, 0}}, {{0, -I}, {I, 0}}, {{1, 0}, {0, -1}}};
+    memset(O, 0, sizeof(cplx) * 5 * 16);
+    for (int d = 0; d < 4; ++d) O[0][d][d] = 1;
+    c[0] = 1.0;
+    if (s->interaction <= 0) return 1;
+    double n[3] = {ra[0] - rb[0], ra[1] - rb[1], ra[2] - rb[2]};
+    const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int k = 0; k < 3; ++k) n[k] /= len;
+    const int count = s->interaction >= 2 ? 5 : 4;
+    for (int A = 1; A < count; ++A) {
+        for (int u = 0; u < 2; ++u)
+            for (int v = 0; v < 2; ++v) {
+                cplx val = 0;
+                if (A <= 3)
+                    val = sig[A - 1][u][v];
+                else
+                    for (int k = 0; k < 3; ++k) val += n[k] * sig[k][u][v];
+                O[A][u][2 + v] = val;  /* L rows, S columns */
+                O[A][2 + u][v] = val;  /* S rows, L columns */
+            }
+        c[A] = -0.5;
+    }
+    return count;
+}
+
+static cplx trace_of_product(int n_mat, cplx (*const *mats)[4])
+{
+    cplx acc[4][4], tmp[4][4];
+    memcpy(acc, mats[0], sizeof(acc));
+    for (int k = 1; k < n_mat; ++k) {
+        matmul4(acc, (cplx(*)[4])mats[k], tmp);
+        memcpy(acc, tmp, sizeof(acc));
+    }
+    return trace4(acc);
+}
+
+/* f(r1,r2,r3,r4,tau) * r12 * r34 at one sample, the two integrands of the
+ * trace-form Eq. MCMP2:  -1/2 { tr[G-31 G+13] tr[G-42 G+24] - tr[G-31 G+14 G-42 G+23] }.
+ * With the Gaunt / Breit terms each point x carries the operator of its electron
+ * pair's interaction term where the two propagators meet at x: for terms A of
+ * g(1,2) and B of g(3,4),
+ *   direct   tr[G-31 O_A G+13 O_B] tr[G-42 O_A G+24 O_B],
+ *   exchange tr[G-31 O_A G+14 O_B G-42 O_A G+23 O_B],
+ * summed with c_A c_B. */
+static cplx integrand(const or_system *s, const cplx *p1, const cplx *p2, const cplx *p3,
+                      const cplx *p4, double tau, const double *r1, const double *r2, const double *r3,
+                      const double *r4)
+{
+    if (s->interaction > 0) {
+        cplx Gm31[4][4], Gp13[4][4], Gm42[4][4], Gp24[4][4], Gp14[4][4], Gp23[4][4];
+        green(s, p3, p1, tau, -1, Gm31);
+        green(s, p1, p3, tau, +1, Gp13);
+        green(s, p4, p2, tau, -1, Gm42);
+        green(s, p2, p4, tau, +1, Gp24);
+        green(s, p1, p4, tau, +1, Gp14);
+        green(s, p2, p3, tau, +1, Gp23);
+        cplx OA[5][4][4], OB[5][4][4];
+        double cA[5], cB[5];
+        const int nA = interaction_terms(s, r1, r2, OA, cA);
+        const int nB = interaction_terms(s, r3, r4, OB, cB);
+        cplx direct = 0, exchange = 0;
+        for (int A = 0; A < nA; ++A)
+            for (int B = 0; B < nB; ++B) {
+                cplx (*const d1[4])[4] = {Gm31, OA[A], Gp13, OB[B]};
+                cplx (*const d2[4])[4] = {Gm42, OA[A], Gp24, OB[B]};
+                cplx (*const x[8])[4] = {Gm31, OA[A], Gp14, OB[B], Gm42, OA[A], Gp23, OB[B]};
+                direct += cA[A] * cB[B] * trace_of_product(4, d1) * trace_of_product(4, d2);
+                exchange += cA[A] * cB[B] * trace_of_product(8, x);
+            }
+        return -0.5 * (direct - exchange);
+    }
+    (void)r1;
+    (void)r2;
+    (void)r3;
+    (void)r4;
     cplx Gm31[4][4], Gp13[4][4], Gm42[4][4], Gp24[4][4], Gp14[4][4], Gp23[4][4];
     green(s, p3, p1, tau, -1, Gm31);
     green(s, p1, p3, tau, +1, Gp13);
@@ -278,9 +358,10 @@ static cplx integrand(const or_system *s, const cplx *p1, const cplx *p2, const 
  * the weights.  out = {Re, Im}. */
 static cplx quotient(const or_system *s, const cplx *p1, const cplx *p2, const cplx *p3,
                      const cplx *p4, double g1, double g2, double g3, double g4, double tau,
-                     double Ng, double lambda)
+                     double Ng, double lambda, const double *r1, const double *r2, const double *r3,
+                     const double *r4)
 {
-    const cplx F = integrand(s, p1, p2, p3, p4, tau);
+    const cplx F = integrand(s, p1, p2, p3, p4, tau, r1, r2, r3, r4);
     return F * (Ng / (g1 * g2)) * (Ng / (g3 * g4)) * (exp(lambda * tau) / lambda);
 }
 
@@ -297,7 +378,7 @@ void or_pair_value(const or_system *s, const double *r1, const double *r2, const
     }
     const cplx *P = (const cplx *)phi;
     const cplx v = quotient(s, P, P + 4 * n, P + 8 * n, P + 12 * n, g[0], g[1], g[2], g[3], tau,
-                            or_Ng(s), or_lambda(s));
+                            or_Ng(s), or_lambda(s), r1, r2, r3, r4);
     out[0] = creal(v);
     out[1] = cimag(v);
     free(phi);
@@ -343,7 +424,8 @@ int or_eval_steps(const or_system *s, long n_steps, int m, int n_tau, const doub
     double *part = malloc(sizeof(double) * m);
     double *apart = malloc(sizeof(double) * m);
     for (long st = 0; st < n_steps; ++st) {
-        positions_prepare(s, m, r + (size_t)st * m * 6, phi, g, n_threads);
+        const double *rs = r + (size_t)st * m * 6;
+        positions_prepare(s, m, rs, phi, g, n_threads);
         kahan tot = {0, 0}, atot = {0, 0};
         for (int t = 0; t < n_tau; ++t) {
             const double tt = tau[st * n_tau + t];
@@ -355,7 +437,8 @@ int or_eval_steps(const or_system *s, long n_steps, int m, int n_tau, const doub
                     const cplx *p3 = phi + (size_t)(2 * q) * 4 * n;
                     const cplx *p4 = phi + (size_t)(2 * q + 1) * 4 * n;
                     const double v = creal(quotient(s, p1, p2, p3, p4, g[2 * p], g[2 * p + 1],
-                                                    g[2 * q], g[2 * q + 1], tt, Ng, lambda));
+                                                    g[2 * q], g[2 * q + 1], tt, Ng, lambda, rs + 6 * p,
+                                                    rs + 6 * p + 3, rs + 6 * q, rs + 6 * q + 3));
                     kadd(&acc, v);
                     kadd(&aacc, fabs(v));
                 }
@@ -403,7 +486,8 @@ int or_eval_pairs(const or_system *s, int m, int n_tau, const double *r, const d
             out[(size_t)k * n_tau + t] =
                 creal(quotient(s, phi + (size_t)(2 * p) * 4 * n, phi + (size_t)(2 * p + 1) * 4 * n,
                                phi + (size_t)(2 * q) * 4 * n, phi + (size_t)(2 * q + 1) * 4 * n,
-                               g[2 * p], g[2 * p + 1], g[2 * q], g[2 * q + 1], tau[t], Ng, lambda));
+                               g[2 * p], g[2 * p + 1], g[2 * q], g[2 * q + 1], tau[t], Ng, lambda,
+                               r + 6 * p, r + 6 * p + 3, r + 6 * q, r + 6 * q + 3));
     }
     free(phi);
     free(g);

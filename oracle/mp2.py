@@ -85,6 +85,45 @@ def spinor_eri(oracle) -> np.ndarray:
     return V.reshape(n, n, n, n)
 
 
+def mixed_function_pairs(n_l: int) -> np.ndarray:
+    """Pairs (value function, gradient function) that occur in densities phi_k^dag alpha phi_l:
+    alpha couples the large components (values) with the small ones (gradients)."""
+    large = [4 * mu for mu in range(n_l)]
+    small = [4 * mu + j for mu in range(n_l) for j in (1, 2, 3)]
+    return np.array([(p, q) for p in large for q in small], dtype=np.int32)
+
+
+def alpha_matrices() -> np.ndarray:
+    """alpha_x, alpha_y, alpha_z in the component order (L-alpha, L-beta, S-alpha, S-beta):
+    sigma_k in the off-diagonal 2 x 2 blocks."""
+    A = np.zeros((3, 4, 4), dtype=np.complex128)
+    for k in range(3):
+        A[k, 0:2, 2:4] = PAULI[k]
+        A[k, 2:4, 0:2] = PAULI[k]
+    return A
+
+
+def spinor_eri_gaunt(oracle) -> np.ndarray:
+    """V[k, l, m, n] = (kl|mn) - 1/2 sum_j (kl|alpha_j . alpha_j|mn): the spinor integrals of the
+    Coulomb + Gaunt interaction 1/r12 - alpha(1).alpha(2)/(2 r12) (Sec. II) in chemists' notation.
+    The Gaunt densities rho^j_kl = phi_k^dag alpha_j phi_l are expanded over (value, gradient)
+    function pairs and contracted with their Coulomb integrals."""
+    system = oracle.system
+    n = system.n_orb
+    U = real_function_coefficients(system)
+    pairs = mixed_function_pairs(system.n_l)
+    J = pair_coulomb_matrix(oracle, pairs)
+    P, Q = pairs[:, 0], pairs[:, 1]
+    V = spinor_eri(oracle)
+    for A in alpha_matrices():
+        # f_P f_Q = f_Q f_P: the unordered pair collects both orderings.
+        D = np.einsum("cpk,cd,dpl->klp", U[:, P, :].conj(), A, U[:, Q, :])
+        D += np.einsum("cpk,cd,dpl->klp", U[:, Q, :].conj(), A, U[:, P, :])
+        D = D.reshape(n * n, -1)
+        V = V - 0.5 * (D @ J @ D.T).reshape(n, n, n, n)
+    return V
+
+
 def mp2_energy(system, V: np.ndarray) -> float:
     """E2 = 1/2 sum_{ij occ} sum_{ab vir} (ia|jb)[(ai|bj) - (bi|aj)] / (e_i + e_j - e_a - e_b)."""
     o, v = system.n_occ, system.n_vir

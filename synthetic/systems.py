@@ -261,14 +261,20 @@ _SOFT_ZN = [(0, 0.05, 2.5, 5), (1, 0.05, 2.5, 4)]                  # 5 + 12 = 17
 _SOFT_H = [(0, 0.08, 2.5, 3)]                                        # 3
 
 
-def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = False) -> System:
+def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = False,
+                small_scale: float | None = None) -> System:
     """Draw one of the synthetic systems.
 
     config: "tiny" (Z=30 + Z=1, n_L = 20, 4 occ / 16 vir),
             "medium" (4 x Z=50 + 2 x Z=17, n_L = 300, 80 occ / 400 vir),
             "adjoint" (Z=50 + 2 x Z=17, n_L = 120, 24 occ / 120 vir),
             "size" (n_units x (Z=80 + 2 x Z=17), n_L = 110 per unit,
-                    40 occ / 180 vir per unit)."""
+                    40 occ / 180 vir per unit).
+    small_scale: factor on the random small-component coefficients before
+    orthonormalisation (default 1/(2c), the kinetic-balance size); a test
+    system with small_scale = 1 has small components of order one, so terms
+    that couple large and small components (the Gaunt/Breit interaction) are
+    of the size of the Coulomb ones."""
     rng = np.random.default_rng(seed)
     charges, centres = _geometry(config, n_units)
     shells = []
@@ -306,7 +312,7 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     eps = np.repeat(eps_pairs, 2)
 
     half = rng.standard_normal((4 * n_l, n_orb // 2)) + 1j * rng.standard_normal((4 * n_l, n_orb // 2))
-    half[2 * n_l:] *= 1.0 / (2.0 * SPEED_OF_LIGHT)
+    half[2 * n_l:] *= (1.0 / (2.0 * SPEED_OF_LIGHT)) if small_scale is None else float(small_scale)
     # Per-entry spread: each basis function counts with unit norm, and an
     # orbital of energy eps draws mostly on functions whose exponent matches
     # its spatial extent (alpha ~ 0.57 |eps|, the best single Gaussian for a
@@ -328,6 +334,8 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     name = config if config != "size" else f"size{n_units}"
     if soft:
         name += "-soft"
+    if small_scale is not None:
+        name += f"-small{small_scale:g}"
     return System(name=name, centres=np.ascontiguousarray(centres, dtype=np.float64),
                   charges=np.array(charges, dtype=np.int32), shell_centre=shell_centre,
                   shell_l=shell_l, shell_alpha=shell_alpha, shell_coef=shell_coef,
