@@ -107,11 +107,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_oracle_rate(system, m_sample, n_tau, seed=1, steps=1, n_threads=None):
+def cpu_oracle_rate(system, m_sample, n_tau, seed=1, steps=1, n_threads=None, interaction=0):
     """Pair-pair samples/s of the oracle on this host's cores (bounded sample)."""
     import oracle
     import synthetic
-    orc = oracle.Oracle(system, n_threads=n_threads)
+    orc = oracle.Oracle(system, n_threads=n_threads, interaction=interaction)
     r = synthetic.walker_positions(system.centres, steps, m_sample, seed=seed)
     tau = synthetic.imaginary_times(orc.lam(), steps, n_tau, seed=seed + 1)
     t0 = time.perf_counter()
@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "tf32", "fp64"], default="mixed")
+    ap.add_argument("--interaction", choices=["coulomb", "gaunt", "breit"], default="coulomb",
+                    help="two-electron operator of Sec. II (Gaunt / Breit terms: FP64 form only)")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form beside the mixed run")
     ap.add_argument("--tf32-steps", type=int, default=200, help="timed steps of the TF32 form beside the mixed run")
     ap.add_argument("--stat-steps", type=int, default=10000, help="steps of the run that estimates sigma for time-to-0.1%%")
@@ -215,6 +217,8 @@ def main():
     system = synthetic.make_system("medium")
     peaks, peak_kind = load_peaks()
     prec = {"mixed": pkg.MCMP2_MIXED, "tf32": pkg.MCMP2_TF32, "fp64": pkg.MCMP2_FP64}[args.precision]
+    inter = {"coulomb": pkg.MCMP2_COULOMB, "gaunt": pkg.MCMP2_GAUNT, "breit": pkg.MCMP2_BREIT}[args.interaction]
+    assert inter == pkg.MCMP2_COULOMB or prec == pkg.MCMP2_FP64, "the Gaunt / Breit terms run in the FP64 form"
     seed = 5632 + rank
     m_run = args.m
     samples_per_step = m_run * (m_run - 1) // 2 * N_TAU
@@ -223,6 +227,8 @@ def main():
 
     def make_ctx(p):
         ctx = pkg.Context(system, m_run, N_TAU, p, device=local)
+        if p == pkg.MCMP2_FP64 and inter != pkg.MCMP2_COULOMB:
+            ctx.set_interaction(inter)
         r0 = synthetic.walker_positions(system.centres, 1, m_run, seed=seed)[0]
         ctx.set_walkers(r0, seed, 200)
         return ctx
@@ -367,13 +373,15 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, dt, n, cores = cpu_oracle_rate(system, args.cpu_sample_m, N_TAU, steps=args.cpu_sample_steps)
-        rate1, dt1, n1, _ = cpu_oracle_rate(system, 128, N_TAU, seed=3, n_threads=1)
+        rate, dt, n, cores = cpu_oracle_rate(system, args.cpu_sample_m, N_TAU, steps=args.cpu_sample_steps,
+                                             interaction=inter)
+        rate1, dt1, n1, _ = cpu_oracle_rate(system, 128 if inter == 0 else 32, N_TAU, seed=3, n_threads=1,
+                                            interaction=inter)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_sample_steps} step(s) of m={args.cpu_sample_m} walker pairs x {N_TAU} tau of the "
                          f"medium system ({n} pair-pair samples, {dt:.1f} s)",
                "one_core": {"value": rate1, "unit": UNIT, "cores": 1,
-                            "sample": f"one step of m=128 x {N_TAU} tau ({n1} samples, {dt1:.1f} s)"}}
+                            "sample": f"one step of m={128 if inter == 0 else 32} x {N_TAU} tau ({n1} samples, {dt1:.1f} s)"}}
 
     if rank == 0:
         line = {
@@ -382,7 +390,8 @@ def main():
             "vs_baseline": None, "dtype": {pkg.MCMP2_MIXED: "bf16x3", pkg.MCMP2_TF32: "tf32"}.get(prec, "f64"),
             "data": "synthetic",
             "config": {"workload": WORKLOAD if m_run == M else WORKLOAD.replace("m=1024", f"m={m_run}"),
-                       "precision": args.precision, "l2": "flushed between timed steps",
+                       "precision": args.precision, "interaction": args.interaction,
+                       "l2": "flushed between timed steps",
                        "parallelism": f"{world} independent replicas"},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": m_run * 6 * 8 + N_TAU * 8,

@@ -66,6 +66,13 @@ extern "C" {
                         * operands rounded to nearest TF32 (10-bit significand): 2/3 of the MMAs,
                         * relative error per operand <= 2^-11, unbiased */
 
+/* Two-electron interaction (Sec. II, operator g_ij).  The paper's runs keep the
+ * Coulomb term only; the Gaunt term -alpha(i).alpha(j)/(2 r_ij) and the gauge
+ * term -(alpha(i).r_ij)(alpha(j).r_ij)/(2 r_ij^3) (together: Breit) can be added. */
+#define MCMP2_COULOMB 0
+#define MCMP2_GAUNT 1  /* Coulomb + Gaunt */
+#define MCMP2_BREIT 2  /* Coulomb + Gaunt + gauge term */
+
 /* Sampling constants (Sec. III leaves them open; see the library design notes). */
 #define MCMP2_DELTA0 0.6        /* initial Metropolis displacement (bohr) */
 #define MCMP2_ADAPT_WINDOW 20   /* burn-in steps per displacement adaptation */
@@ -112,6 +119,15 @@ typedef struct {
  * (MCMP2_FP64, MCMP2_MIXED or MCMP2_TF32).  Fails with MCMP2_EUNSUPPORTED on
  * devices other than compute capability 10.3. */
 int mcmp2_create(mcmp2_ctx **ctx, int device, void *cuda_stream, int precision);
+
+/* Select the two-electron interaction of the integrand (MCMP2_COULOMB, the default,
+ * MCMP2_GAUNT or MCMP2_BREIT) for the following steps and replays.  Each electron pair's
+ * interaction (1/r_ab) sum_A c_A O_A(a) O_A(b), O_A in {1, alpha_x, alpha_y, alpha_z,
+ * alpha.n_ab}, enters the trace form with O_A at the two points of the pair (the
+ * weight's 1/r_ab is unchanged).  FP64 form only: MCMP2_EUNSUPPORTED in the tensor-core
+ * forms for anything but MCMP2_COULOMB; mcmp2_backward requires MCMP2_COULOMB.
+ * Statistics accumulated so far are kept; checkpoints record the interaction. */
+int mcmp2_set_interaction(mcmp2_ctx *ctx, int interaction);
 
 /* Release the context (not the caller's workspace).  NULL is ignored. */
 void mcmp2_destroy(mcmp2_ctx *ctx);

@@ -21,6 +21,9 @@ MCMP2_OK = 0
 MCMP2_FP64 = 0
 MCMP2_MIXED = 1
 MCMP2_TF32 = 2
+MCMP2_COULOMB = 0
+MCMP2_GAUNT = 1
+MCMP2_BREIT = 2
 STATUS = {-1: "EINVAL", -2: "ENOTLOADED", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT", -6: "ENOSPACE",
           -7: "EUNSUPPORTED"}
 
@@ -76,6 +79,7 @@ SIGNATURES = {
     "mcmp2_debug_partials": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mcmp2_profile": (_I, [_P, _I, ctypes.POINTER(ProfileCounters)]),
     "mcmp2_test_stall_next": (_I, [_P, ctypes.c_double]),
+    "mcmp2_set_interaction": (_I, [_P, _I]),
     "mcmp2_checkpoint_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "mcmp2_pair_sum_f64_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, ctypes.c_double, _P, _P]),
     "mcmp2_checkpoint": (_I, [_P, _P, _SZ]),
@@ -258,6 +262,10 @@ class Context:
         pc = ProfileCounters()
         self._check(self.lib.mcmp2_profile(self.h, int(mode), ctypes.byref(pc) if mode == 0 else None))
         return {k: getattr(pc, k) for k, _ in pc._fields_} if mode == 0 else None
+
+    def set_interaction(self, interaction: int):
+        """MCMP2_COULOMB (default), MCMP2_GAUNT or MCMP2_BREIT for the following steps (FP64 form)."""
+        self._check(self.lib.mcmp2_set_interaction(self.h, int(interaction)))
 
     def test_stall_next(self, wait_limit_s: float):
         """Test hook: the next contraction launch withholds its first copy (bounded wait runs out)."""

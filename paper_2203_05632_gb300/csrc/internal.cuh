@@ -36,6 +36,7 @@ struct DevSystem {
     double eps_homo, eps_lumo, lambda, Ng;
     const double *WL;          // FP64 large operand [n_l][2][n_orb][2] (L-alpha, L-beta; re, im)
     const double *WS;          // FP64 small operand [3 n_l][2][n_orb][2] (S-alpha, S-beta)
+    int interaction;           // MCMP2_COULOMB, MCMP2_GAUNT or MCMP2_BREIT (FP64 form only)
 };
 
 // ---------------------------------------------------------------------------
@@ -123,8 +124,9 @@ cudaError_t launch_basis(const DevSystem &s, const double *r, T *B, cudaStream_t
 
 cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi, cudaStream_t st);
 cudaError_t prepare_f64();  // sets the FP64 contraction kernel's shared-memory limit
+// r (positions [m][2][3]) is read for the Breit gauge term only; it may be null otherwise.
 cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale,
-                             const double *a, double *partials, cudaStream_t st);
+                             const double *a, double *partials, cudaStream_t st, const double *r = nullptr);
 
 size_t adjoint_smem_bytes();
 cudaError_t launch_adjoint_time(const DevSystem &s, const double *B, const double *phi, const double *scale,

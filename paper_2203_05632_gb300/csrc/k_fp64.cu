@@ -154,14 +154,154 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b)  // conj(a) * b
     return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
+// ---------------------------------------------------------------------------
+// Gaunt and Breit terms of the interaction (Sec. II):
+//   g(a,b) = 1/r_ab - alpha(a).alpha(b) / (2 r_ab) - (alpha(a).r_ab)(alpha(b).r_ab) / (2 r_ab^3)
+//          = (1/r_ab) sum_A c_A O_A(a) O_A(b),
+// O_0 = 1 (c = 1); O_k = alpha_k, k = x, y, z (c = -1/2); O_n = alpha.n with n the
+// unit vector from b to a (c = -1/2, Breit only).  alpha.v has sigma.v in its
+// off-diagonal 2x2 blocks (components L-alpha, L-beta, S-alpha, S-beta).  The
+// operator of each electron pair sits where the two propagators meet at its
+// points:  direct  tr[G-(1q,1p) O_A G+(1p,1q) O_B] tr[G-(2q,2p) O_A G+(2p,2q) O_B],
+//          exchange tr[G-(1q,1p) O_A G+(1p,2q) O_B G-(2q,2p) O_A G+(2p,1q) O_B],
+// summed over the terms A of pair p and B of pair q with c_A c_B.
+// ---------------------------------------------------------------------------
+struct InteractionTerm {
+    bool identity;
+    double v[3];  // alpha.v
+    double c;
+};
+
+// Y = X O for a 4x4 complex X (row-major) and O = 1 or alpha.v.
+__device__ __forceinline__ void rmul_op(const double2 *X, const InteractionTerm &o, double2 *Y)
+{
+    if (o.identity) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) Y[j] = X[j];
+        return;
+    }
+    const double2 s00 = make_double2(o.v[2], 0.0), s01 = make_double2(o.v[0], -o.v[1]);
+    const double2 s10 = make_double2(o.v[0], o.v[1]), s11 = make_double2(-o.v[2], 0.0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double2 x0 = X[4 * c], x1 = X[4 * c + 1], x2 = X[4 * c + 2], x3 = X[4 * c + 3];
+        const double2 a0 = cmul(x2, s00), a1 = cmul(x3, s10), b0 = cmul(x2, s01), b1 = cmul(x3, s11);
+        const double2 c0 = cmul(x0, s00), c1 = cmul(x1, s10), d0 = cmul(x0, s01), d1 = cmul(x1, s11);
+        Y[4 * c] = make_double2(a0.x + a1.x, a0.y + a1.y);
+        Y[4 * c + 1] = make_double2(b0.x + b1.x, b0.y + b1.y);
+        Y[4 * c + 2] = make_double2(c0.x + c1.x, c0.y + c1.y);
+        Y[4 * c + 3] = make_double2(d0.x + d1.x, d0.y + d1.y);
+    }
+}
+
+__device__ __forceinline__ void matmul44(const double2 *A, const double2 *B, double2 *C)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double2 t = cmul(A[4 * i + k], B[4 * k + j]);
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+            C[4 * i + j] = acc;
+        }
+}
+
+// tr[X Y]
+__device__ __forceinline__ double2 trace_prod(const double2 *X, const double2 *Y)
+{
+    double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double2 u = cmul(X[4 * i + j], Y[4 * j + i]);
+            t.x += u.x;
+            t.y += u.y;
+        }
+    return t;
+}
+
+__device__ int interaction_terms(int interaction, const double *r, int p, InteractionTerm *t)
+{
+    t[0].identity = true;
+    t[0].c = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        t[1 + k].identity = false;
+        t[1 + k].c = -0.5;
+        t[1 + k].v[0] = k == 0;
+        t[1 + k].v[1] = k == 1;
+        t[1 + k].v[2] = k == 2;
+    }
+    if (interaction < 2) return 4;
+    const double dx = r[6 * p] - r[6 * p + 3], dy = r[6 * p + 1] - r[6 * p + 4], dz = r[6 * p + 2] - r[6 * p + 5];
+    const double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+    t[4].identity = false;
+    t[4].c = -0.5;
+    t[4].v[0] = dx * inv;
+    t[4].v[1] = dy * inv;
+    t[4].v[2] = dz * inv;
+    return 5;
+}
+
+// Real part of -1/2 (direct - exchange) with the Gaunt (interaction 1) or Breit (2)
+// terms.  M1 = G-(1p,1q), M3 = G-(2p,2q), N11 = G+(1p,1q), N22 = G+(2p,2q),
+// M2 = G+(1p,2q), M4 = G+(2p,1q); G-(y,x) = G-(x,y)^dagger.
+__device__ __noinline__ double breit_value(int interaction, const double2 *M1, const double2 *M3, const double2 *N11,
+                                           const double2 *N22, const double2 *M2, const double2 *M4, const double *r,
+                                           int p, int q)
+{
+    InteractionTerm tp[5], tq[5];
+    const int np = interaction_terms(interaction, r, p, tp);
+    const int nq = interaction_terms(interaction, r, q, tq);
+    double2 M1h[16], M3h[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            M1h[4 * i + j] = make_double2(M1[4 * j + i].x, -M1[4 * j + i].y);
+            M3h[4 * i + j] = make_double2(M3[4 * j + i].x, -M3[4 * j + i].y);
+        }
+    double2 direct = make_double2(0.0, 0.0), exchange = make_double2(0.0, 0.0);
+    double2 QB[16], SB[16], PA[16], RA[16], U[16], W1[16], W2[16];
+    for (int B = 0; B < nq; ++B) {
+        rmul_op(N11, tq[B], QB);
+        rmul_op(N22, tq[B], SB);
+        for (int A = 0; A < np; ++A) {
+            const double c = tp[A].c * tq[B].c;
+            rmul_op(M1h, tp[A], PA);
+            rmul_op(M3h, tp[A], RA);
+            const double2 d = cmul(trace_prod(PA, QB), trace_prod(RA, SB));
+            direct.x += c * d.x;
+            direct.y += c * d.y;
+            matmul44(PA, M2, U);
+            rmul_op(U, tq[B], W1);
+            matmul44(RA, M4, U);
+            rmul_op(U, tq[B], W2);
+            const double2 x = trace_prod(W1, W2);
+            exchange.x += c * x.x;
+            exchange.y += c * x.y;
+        }
+    }
+    return -0.5 * (direct.x - exchange.x);
+}
+
 // One CTA per (tile, tau).  Rows of a tile side are (position, component)
 // = 4 x_local + c with x_local = 2 p_local + e.  Threads 0..127 own the
 // same-electron position blocks (G- and G+), threads 128..255 the cross ones
 // (G+ only, since the trace form uses G- only between like electrons).
+// WITH_TERMS: the Gaunt / Breit terms (a separate instance keeps the Coulomb
+// kernel's registers and stack untouched).
+template <bool WITH_TERMS>
 __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const double2 *__restrict__ phi,
                                                            const double *__restrict__ scale,
                                                            const double *__restrict__ a,
-                                                           double *__restrict__ partials, int n_tiles)
+                                                           double *__restrict__ partials, int n_tiles,
+                                                           const double *__restrict__ r)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     F64Smem &sm = *reinterpret_cast<F64Smem *>(smem_raw);
@@ -282,7 +422,8 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
                     ex.x += w.x;
                     ex.y += w.y;
                 }
-            const double F = -0.5 * (direct.x - ex.x);  // real part of -1/2 (direct - exchange)
+            double F = -0.5 * (direct.x - ex.x);  // real part of -1/2 (direct - exchange)
+            if constexpr (WITH_TERMS) F = breit_value(s.interaction, M1, M3, N11, N22, M2, M4, r, p, q);
             v = F * a[p] * a[q] / s.lambda;
         }
         sm.part[tid] = v;
@@ -299,15 +440,19 @@ static bool g_f64_configured = false;
 
 cudaError_t prepare_f64()
 {
-    const cudaError_t e =
-        cudaFuncSetAttribute(pairs_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F64Smem));
+    cudaError_t e =
+        cudaFuncSetAttribute(pairs_f64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F64Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pairs_f64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(F64Smem));
     if (e == cudaSuccess) g_f64_configured = true;
     return e;
 }
 
 cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale, const double *a,
-                             double *partials, cudaStream_t st)
+                             double *partials, cudaStream_t st, const double *r)
 {
+    if (s.interaction >= 2 && !r) return cudaErrorInvalidValue;
     const size_t smem = sizeof(F64Smem);
     if (!g_f64_configured) {
         const cudaError_t e = prepare_f64();
@@ -315,8 +460,12 @@ cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double
     }
     const int n_tiles = n_tiles_for(s.m, F64_TP);
     dim3 grid(n_tiles, s.n_tau);
-    pairs_f64_kernel<<<grid, 256, smem, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, a, partials,
-                                              n_tiles);
+    if (s.interaction > 0)
+        pairs_f64_kernel<true><<<grid, 256, smem, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, a,
+                                                        partials, n_tiles, r);
+    else
+        pairs_f64_kernel<false><<<grid, 256, smem, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, a,
+                                                         partials, n_tiles, r);
     return cudaGetLastError();
 }
 

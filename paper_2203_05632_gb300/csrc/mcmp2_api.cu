@@ -101,6 +101,7 @@ uint64_t fnv1a(uint64_t h, const void *data, size_t n)
     return h;
 }
 
+
 const int NCART[3] = {1, 3, 6};
 const int CART[3][6][3] = {
     {{0, 0, 0}},
@@ -124,6 +125,7 @@ struct mcmp2_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int precision = MCMP2_FP64;
+    int interaction = MCMP2_COULOMB;
     std::string err;
     bool bound = false, loaded = false, walkers = false;
     mcmp2_dims dims{};
@@ -409,6 +411,7 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     S.Ng = Ng;
     S.WL = ctx->at<double>(L.WL);
     S.WS = ctx->at<double>(L.WS);
+    S.interaction = ctx->interaction;
 
     uint64_t h = 1469598103934665603ull;
     h = fnv1a(h, b->centres, sizeof(double) * 3 * b->n_centres);
@@ -497,7 +500,7 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         CK(launch_basis<double>(S, r, B, st), "basis values");
         CK(launch_spinors_f64(S, B, phi, st), "spinor formation");
         if (e0) CK(record_event(e0, st), "event");
-        CK(launch_pairs_f64(S, phi, scale, a, partials, st), "pair-of-pairs tiles");
+        CK(launch_pairs_f64(S, phi, scale, a, partials, st, r), "pair-of-pairs tiles");
         if (e1) CK(record_event(e1, st), "event");
         ctx->launches += 4;
         ctx->pair_launches += 1;
@@ -703,6 +706,8 @@ int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
     if (ctx->precision != MCMP2_FP64) return ctx->fail(MCMP2_EUNSUPPORTED, "the adjoint runs in the FP64 form");
+    if (ctx->interaction != MCMP2_COULOMB)
+        return ctx->fail(MCMP2_EUNSUPPORTED, "the adjoint covers the Coulomb interaction");
     if (n < 1 || !r_host || !tau_host || !d_eps_host || !d_C_host) return ctx->fail(MCMP2_EINVAL, "bad backward arguments");
     const int m = ctx->dims.m, nt = ctx->dims.n_tau;
     if (!all_finite(r_host, (size_t)n * m * 6)) return ctx->fail(MCMP2_ENONFINITE, "non-finite position");
@@ -856,6 +861,19 @@ int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out)
     return MCMP2_OK;
 }
 
+int mcmp2_set_interaction(mcmp2_ctx *ctx, int interaction)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (interaction != MCMP2_COULOMB && interaction != MCMP2_GAUNT && interaction != MCMP2_BREIT)
+        return ctx->fail(MCMP2_EINVAL, "unknown interaction");
+    if (interaction != MCMP2_COULOMB && ctx->precision != MCMP2_FP64)
+        return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt and Breit terms run in the FP64 form");
+    ctx->interaction = interaction;
+    ctx->sys.interaction = interaction;
+    ctx->drop_graph();  // the captured step holds the system by value
+    return MCMP2_OK;
+}
+
 int mcmp2_test_stall_next(mcmp2_ctx *ctx, double wait_limit_s)
 {
     if (!ctx) return MCMP2_EINVAL;
@@ -865,6 +883,16 @@ int mcmp2_test_stall_next(mcmp2_ctx *ctx, double wait_limit_s)
     ctx->drop_graph();  // the next step is issued directly, not replayed
     return MCMP2_OK;
 }
+
+namespace {
+// Digest a checkpoint carries: the system's, extended by the interaction, so a
+// walk restores only into the same system with the same integrand.
+uint64_t run_digest(const mcmp2_ctx *ctx)
+{
+    if (ctx->interaction == MCMP2_COULOMB) return ctx->digest;  // unchanged for the paper's operator
+    return fnv1a(ctx->digest, &ctx->interaction, sizeof(ctx->interaction));
+}
+}  // namespace
 
 int mcmp2_checkpoint_bytes(const mcmp2_ctx *ctx, size_t *bytes)
 {
@@ -884,7 +912,7 @@ int mcmp2_checkpoint(mcmp2_ctx *ctx, void *buf, size_t capacity)
     ck.magic = CK_MAGIC;
     ck.version = 1;
     ck.dims = ctx->dims;
-    ck.digest = ctx->digest;
+    ck.digest = run_digest(ctx);
     ck.delta = ctx->delta;
     cudaStream_t st = ctx->stream;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -907,7 +935,8 @@ int mcmp2_restore(mcmp2_ctx *ctx, const void *buf, size_t bytes)
     std::memcpy(&ck, buf, sizeof(ck));
     if (ck.magic != CK_MAGIC || ck.version != 1) return ctx->fail(MCMP2_EINVAL, "not a checkpoint");
     if (std::memcmp(&ck.dims, &ctx->dims, sizeof(mcmp2_dims)) != 0) return ctx->fail(MCMP2_EINVAL, "dims differ");
-    if (ck.digest != ctx->digest) return ctx->fail(MCMP2_EINVAL, "checkpoint belongs to another system");
+    if (ck.digest != run_digest(ctx))
+        return ctx->fail(MCMP2_EINVAL, "checkpoint belongs to another system or interaction");
     const size_t need = sizeof(Checkpoint) + sizeof(double) * 6 * (size_t)ctx->dims.m;
     if (bytes < need) return ctx->fail(MCMP2_EINVAL, "checkpoint truncated");
     const double *r = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof(Checkpoint));
