@@ -44,11 +44,12 @@ TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 PAIRS_TRAFFIC_BYTES = {"mixed": 138.1e6, "tf32": 138.3e6}
 
 
-def flops_per_sample(n_occ, n_vir):
-    """Algorithmic flops of one pair-of-pairs sample: the six 4x4 complex propagator
-    blocks the trace form needs (two G- over n_occ, four G+ over n_vir), 8 flops
-    per complex multiply-add."""
-    return 8 * (2 * 16 * n_occ + 4 * 16 * n_vir)
+def flops_per_sample(n_occ, n_vir, n_comp=4):
+    """Algorithmic flops of one pair-of-pairs sample: the six n_comp x n_comp complex
+    propagator blocks the trace form needs (two G- over n_occ, four G+ over n_vir),
+    8 flops per complex multiply-add."""
+    nn = n_comp * n_comp
+    return 8 * (2 * nn * n_occ + 4 * nn * n_vir)
 
 
 def load_peaks():
@@ -185,6 +186,8 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "tf32", "fp64"], default="mixed")
     ap.add_argument("--interaction", choices=["coulomb", "gaunt", "breit"], default="coulomb",
                     help="two-electron operator of Sec. II (Gaunt / Breit terms: FP64 form only)")
+    ap.add_argument("--components", type=int, choices=[4, 2], default=4,
+                    help="spinor components: 4, or 2 for the two-component variant (FP64 form only)")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form beside the mixed run")
     ap.add_argument("--tf32-steps", type=int, default=200, help="timed steps of the TF32 form beside the mixed run")
     ap.add_argument("--stat-steps", type=int, default=10000, help="steps of the run that estimates sigma for time-to-0.1%%")
@@ -214,7 +217,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    system = synthetic.make_system("medium")
+    two_c = args.components == 2
+    assert not two_c or args.precision == "fp64", "the two-component variant runs in the FP64 form"
+    system = synthetic.make_system("medium", two_component=two_c)
     peaks, peak_kind = load_peaks()
     prec = {"mixed": pkg.MCMP2_MIXED, "tf32": pkg.MCMP2_TF32, "fp64": pkg.MCMP2_FP64}[args.precision]
     inter = {"coulomb": pkg.MCMP2_COULOMB, "gaunt": pkg.MCMP2_GAUNT, "breit": pkg.MCMP2_BREIT}[args.interaction]
@@ -222,7 +227,7 @@ def main():
     seed = 5632 + rank
     m_run = args.m
     samples_per_step = m_run * (m_run - 1) // 2 * N_TAU
-    flop_unit = flops_per_sample(system.n_occ, system.n_vir)
+    flop_unit = flops_per_sample(system.n_occ, system.n_vir, args.components)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     def make_ctx(p):
@@ -389,7 +394,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {pkg.MCMP2_MIXED: "bf16x3", pkg.MCMP2_TF32: "tf32"}.get(prec, "f64"),
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if m_run == M else WORKLOAD.replace("m=1024", f"m={m_run}"),
+            "config": {"workload": (WORKLOAD if m_run == M else WORKLOAD.replace("m=1024", f"m={m_run}"))
+                       + (", two-component spinors (large basis only)" if two_c else ""),
                        "precision": args.precision, "interaction": args.interaction,
                        "l2": "flushed between timed steps",
                        "parallelism": f"{world} independent replicas"},

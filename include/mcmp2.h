@@ -151,6 +151,19 @@ int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, siz
 int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n_vir,
                       const double *C_host, const double *eps_host);
 
+/* Two-component variant (Sec. II: the Monte Carlo algorithm holds unchanged for
+ * two-component Hamiltonians such as X2C).  The spinors have the components
+ * alpha and beta only, phi_k(r) = sum_mu (C^a_{mu k} g_mu(r), C^b_{mu k} g_mu(r)),
+ * so G-(x,y,-tau) and G+(x,y,tau) are 2x2 complex blocks in the same trace form
+ * (a quarter of the four-component contraction work).  C2_host: complex
+ * [2 n_L][n_occ + n_vir] row-major, rows alpha block then beta block; the other
+ * arguments and checks as in mcmp2_load_system.  The result equals
+ * mcmp2_load_system with these rows as L-alpha, L-beta and zero small rows.
+ * FP64 contexts with the Coulomb interaction only (MCMP2_EUNSUPPORTED
+ * otherwise, and from mcmp2_set_interaction and mcmp2_backward afterwards). */
+int mcmp2_load_system_2c(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n_vir,
+                         const double *C2_host, const double *eps_host);
+
 /* Set the m walker pairs from r_host ([m][2][3]), or, if r_host is NULL, draw
  * them from g(r1) g(r2) (each electron from the Gaussian mixture g; Philox
  * counters of the reserved step 2^64 - 1), and run `burn_in` Metropolis

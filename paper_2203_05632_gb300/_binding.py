@@ -24,6 +24,7 @@ MCMP2_TF32 = 2
 MCMP2_COULOMB = 0
 MCMP2_GAUNT = 1
 MCMP2_BREIT = 2
+MCMP2_EUNSUPPORTED = -7
 STATUS = {-1: "EINVAL", -2: "ENOTLOADED", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT", -6: "ENOSPACE",
           -7: "EUNSUPPORTED"}
 
@@ -71,6 +72,7 @@ SIGNATURES = {
     "mcmp2_workspace_bytes": (_I, [ctypes.POINTER(Dims), _I, ctypes.POINTER(_SZ)]),
     "mcmp2_bind_workspace": (_I, [_P, ctypes.POINTER(Dims), _P, _SZ]),
     "mcmp2_load_system": (_I, [_P, ctypes.POINTER(Basis), _I, _I, _P, _P]),
+    "mcmp2_load_system_2c": (_I, [_P, ctypes.POINTER(Basis), _I, _I, _P, _P]),
     "mcmp2_set_walkers": (_I, [_P, _P, _U64, _I64]),
     "mcmp2_run_steps": (_I, [_P, _I64, _U64, ctypes.POINTER(Result)]),
     "mcmp2_eval_fixed": (_I, [_P, _I64, _P, _P, _P]),
@@ -163,12 +165,23 @@ class Context:
         k = self._keep
         self._basis = Basis(len(k[0]), _ptr(k[0]).value, _ptr(k[1]).value, len(k[3]), _ptr(k[2]).value,
                             _ptr(k[3]).value, _ptr(k[4]).value, _ptr(k[5]).value)
-        C = _c(system.C, np.complex128)
-        eps = _c(system.eps, np.float64)
-        self._check(self.lib.mcmp2_load_system(self.h, ctypes.byref(self._basis), int(system.n_occ),
-                                               int(system.n_vir), _ptr(C), _ptr(eps)))
+        self._load(system)
 
     # -- helpers ---------------------------------------------------------
+    def _load(self, sysobj):
+        """mcmp2_load_system, or mcmp2_load_system_2c (alpha and beta rows of C) for a
+        two-component system (``n_comp == 2``, small-component rows of C zero)."""
+        eps = _c(sysobj.eps, np.float64)
+        if getattr(sysobj, "n_comp", 4) == 2:
+            C = _c(sysobj.C[:2 * self.n_l], np.complex128)
+            rc = self.lib.mcmp2_load_system_2c(self.h, ctypes.byref(self._basis), int(sysobj.n_occ),
+                                               int(sysobj.n_vir), _ptr(C), _ptr(eps))
+        else:
+            C = _c(sysobj.C, np.complex128)
+            rc = self.lib.mcmp2_load_system(self.h, ctypes.byref(self._basis), int(sysobj.n_occ),
+                                            int(sysobj.n_vir), _ptr(C), _ptr(eps))
+        self._check(rc)
+
     def _check(self, rc):
         if rc != MCMP2_OK:
             msg = self.lib.mcmp2_last_error(self.h).decode()
@@ -225,10 +238,7 @@ class Context:
         if eps is not None or C is not None:
             sysobj = dataclasses.replace(sysobj, eps=self.system.eps if eps is None else np.asarray(eps),
                                          C=self.system.C if C is None else np.asarray(C))
-        C_ = _c(sysobj.C, np.complex128)
-        eps_ = _c(sysobj.eps, np.float64)
-        self._check(self.lib.mcmp2_load_system(self.h, ctypes.byref(self._basis), int(sysobj.n_occ),
-                                               int(sysobj.n_vir), _ptr(C_), _ptr(eps_)))
+        self._load(sysobj)
         self.system = sysobj
 
     def backward(self, r, tau):

@@ -110,12 +110,14 @@ static cudaError_t gemm_rm(int M, int N, int K, const T *A, int lda, const T *B,
 
 // Spinor values phi[x][c][k] (complex, c = L-alpha, L-beta, S-alpha, S-beta):
 // the large components contract basis values with C^L (Eq. C); the small ones
-// contract the gradients with the Pauli-folded C^S (Eq. KB).
+// contract the gradients with the Pauli-folded C^S (Eq. KB).  Two-component
+// systems (s.n_comp == 2) have the large components only: phi[x][c][k], c =
+// alpha, beta.
 cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi, cudaStream_t st)
 {
-    const int P = 2 * s.m, n4 = 4 * s.n_orb, ld = 8 * s.n_orb;
+    const int P = 2 * s.m, n4 = 4 * s.n_orb, ld = 2 * s.n_comp * s.n_orb;
     cudaError_t e = gemm_rm<double>(P, n4, s.n_l, B, 4 * s.n_l, s.WL, n4, phi, ld, st);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || s.n_comp == 2) return e;
     return gemm_rm<double>(P, n4, 3 * s.n_l, B + s.n_l, 4 * s.n_l, s.WS, n4, phi + n4, ld, st);
 }
 
@@ -136,14 +138,17 @@ __device__ __forceinline__ void tile_coords(int tile, int nb, int &bp, int &bq)
 constexpr int F64_TP = TILE_PAIRS_F64;  // 8 pairs = 16 positions = 64 rows per side
 constexpr int F64_KC = 16;              // orbitals per staged chunk
 
+// NC = 4 components (L-alpha, L-beta, S-alpha, S-beta) or 2 (alpha, beta: the
+// two-component variant); blocks are NC x NC.
+template <int NC>
 struct F64Smem {
-    double2 Gm[2][F64_TP][F64_TP][16];  // G-(x, y) for same-electron position pairs, [e][xp][yp][c*4+d]
+    double2 Gm[2][F64_TP][F64_TP][NC * NC];  // G-(x, y) for same-electron position pairs, [e][xp][yp][c*NC+d]
     union {
         struct {
-            double2 A[F64_KC][64];
-            double2 B[F64_KC][64];
+            double2 A[F64_KC][16 * NC];
+            double2 B[F64_KC][16 * NC];
         } ld;
-        double2 Gp[16][16][16];          // G+(x, y) for all position pairs, [xl][yl][c*4+d]
+        double2 Gp[16][16][NC * NC];          // G+(x, y) for all position pairs, [xl][yl][c*NC+d]
     } u;
     double part[64];
 };
@@ -291,20 +296,22 @@ __device__ __noinline__ double breit_value(int interaction, const double2 *M1, c
 }
 
 // One CTA per (tile, tau).  Rows of a tile side are (position, component)
-// = 4 x_local + c with x_local = 2 p_local + e.  Threads 0..127 own the
+// = NC x_local + c with x_local = 2 p_local + e.  Threads 0..127 own the
 // same-electron position blocks (G- and G+), threads 128..255 the cross ones
 // (G+ only, since the trace form uses G- only between like electrons).
 // WITH_TERMS: the Gaunt / Breit terms (a separate instance keeps the Coulomb
-// kernel's registers and stack untouched).
-template <bool WITH_TERMS>
+// kernel's registers and stack untouched; four components only).
+template <bool WITH_TERMS, int NC>
 __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const double2 *__restrict__ phi,
                                                            const double *__restrict__ scale,
                                                            const double *__restrict__ a,
                                                            double *__restrict__ partials, int n_tiles,
                                                            const double *__restrict__ r)
 {
+    static_assert(NC == 4 || (NC == 2 && !WITH_TERMS), "Gaunt / Breit terms need the small components");
+    constexpr int NN = NC * NC, ROWS = 16 * NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    F64Smem &sm = *reinterpret_cast<F64Smem *>(smem_raw);
+    F64Smem<NC> &sm = *reinterpret_cast<F64Smem<NC> *>(smem_raw);
     const int tile = blockIdx.x, t = blockIdx.y;
     const int nb = pair_blocks(s.m, F64_TP);
     int bp, bq;
@@ -314,18 +321,18 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
     const int xp = i >> 3, yp = i & 7;
     const int xl = 2 * xp + e, yl = 2 * yp + (half ? 1 - e : e);
     const double *sc = scale + (size_t)t * s.n_orb;
-    const int row_base_p = 8 * F64_TP * bp, row_base_q = 8 * F64_TP * bq;
-    const int rows_valid = 8 * s.m;
+    const int row_base_p = ROWS * bp, row_base_q = ROWS * bq;
+    const int rows_valid = 2 * NC * s.m;
 
-    double2 acc[16];
+    double2 acc[NN];
     for (int pass = 0; pass < 2; ++pass) {  // 0: occupied (G-), 1: virtual (G+)
         const int k_begin = pass == 0 ? 0 : s.n_occ;
         const int k_end = pass == 0 ? s.n_occ : s.n_orb;
         const bool active = (pass == 1) || (half == 0);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = make_double2(0.0, 0.0);
+        for (int j = 0; j < NN; ++j) acc[j] = make_double2(0.0, 0.0);
         for (int k0 = k_begin; k0 < k_end; k0 += F64_KC) {
-            for (int idx = tid; idx < F64_KC * 64; idx += 256) {
+            for (int idx = tid; idx < F64_KC * ROWS; idx += 256) {
                 const int row = idx >> 4, kk = idx & 15, k = k0 + kk;
                 double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
                 if (k < k_end) {
@@ -349,17 +356,17 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
             if (active) {
 #pragma unroll 4
                 for (int kk = 0; kk < F64_KC; ++kk) {
-                    double2 xa[4], yb[4];
+                    double2 xa[NC], yb[NC];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) xa[c] = sm.u.ld.A[kk][4 * xl + c];
+                    for (int c = 0; c < NC; ++c) xa[c] = sm.u.ld.A[kk][NC * xl + c];
 #pragma unroll
-                    for (int d = 0; d < 4; ++d) yb[d] = sm.u.ld.B[kk][4 * yl + d];
+                    for (int d = 0; d < NC; ++d) yb[d] = sm.u.ld.B[kk][NC * yl + d];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
+                    for (int c = 0; c < NC; ++c)
 #pragma unroll
-                        for (int d = 0; d < 4; ++d) {
+                        for (int d = 0; d < NC; ++d) {
                             // G(x, y)_cd += X(x)_c conj(X(y)_d)
-                            double2 &g = acc[4 * c + d];
+                            double2 &g = acc[NC * c + d];
                             g.x = fma(xa[c].x, yb[d].x, g.x);
                             g.x = fma(xa[c].y, yb[d].y, g.x);
                             g.y = fma(xa[c].y, yb[d].x, g.y);
@@ -371,11 +378,11 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
         }
         if (pass == 0 && half == 0) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) sm.Gm[e][xp][yp][j] = acc[j];
+            for (int j = 0; j < NN; ++j) sm.Gm[e][xp][yp][j] = acc[j];
         }
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sm.u.Gp[xl][yl][j] = acc[j];
+    for (int j = 0; j < NN; ++j) sm.u.Gp[xl][yl][j] = acc[j];
     __syncthreads();
 
     // Epilogue: one thread per pair of pairs (p, q) of the tile.
@@ -393,7 +400,7 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
             // Direct: tr[G-(1q,1p) G+(1p,1q)] tr[G-(2q,2p) G+(2p,2q)], G-(y,x) = G-(x,y)^dagger.
             double2 t1 = make_double2(0, 0), t2 = make_double2(0, 0);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < NN; ++j) {
                 const double2 u1 = cmulc(M1[j], N11[j]), u2 = cmulc(M3[j], N22[j]);
                 t1.x += u1.x;
                 t1.y += u1.y;
@@ -405,14 +412,14 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
             // = sum_ij (M1^dag M2)_ij (M3^dag M4)_ji.
             double2 ex = make_double2(0, 0);
 #pragma unroll
-            for (int i2 = 0; i2 < 4; ++i2)
+            for (int i2 = 0; i2 < NC; ++i2)
 #pragma unroll
-                for (int j2 = 0; j2 < 4; ++j2) {
+                for (int j2 = 0; j2 < NC; ++j2) {
                     double2 s1 = make_double2(0, 0), s2 = make_double2(0, 0);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const double2 w1 = cmulc(M1[4 * k + i2], M2[4 * k + j2]);
-                        const double2 w2 = cmulc(M3[4 * k + j2], M4[4 * k + i2]);
+                    for (int k = 0; k < NC; ++k) {
+                        const double2 w1 = cmulc(M1[NC * k + i2], M2[NC * k + j2]);
+                        const double2 w2 = cmulc(M3[NC * k + j2], M4[NC * k + i2]);
                         s1.x += w1.x;
                         s1.y += w1.y;
                         s2.x += w2.x;
@@ -440,11 +447,14 @@ static bool g_f64_configured = false;
 
 cudaError_t prepare_f64()
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(pairs_f64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F64Smem));
+    cudaError_t e = cudaFuncSetAttribute(pairs_f64_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(F64Smem<4>));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(pairs_f64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(F64Smem));
+        e = cudaFuncSetAttribute(pairs_f64_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(F64Smem<4>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pairs_f64_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(F64Smem<2>));
     if (e == cudaSuccess) g_f64_configured = true;
     return e;
 }
@@ -453,19 +463,20 @@ cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double
                              double *partials, cudaStream_t st, const double *r)
 {
     if (s.interaction >= 2 && !r) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(F64Smem);
+    if (s.n_comp == 2 && s.interaction > 0) return cudaErrorInvalidValue;
     if (!g_f64_configured) {
         const cudaError_t e = prepare_f64();
         if (e != cudaSuccess) return e;
     }
     const int n_tiles = n_tiles_for(s.m, F64_TP);
     dim3 grid(n_tiles, s.n_tau);
-    if (s.interaction > 0)
-        pairs_f64_kernel<true><<<grid, 256, smem, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, a,
-                                                        partials, n_tiles, r);
+    const double2 *ph = reinterpret_cast<const double2 *>(phi);
+    if (s.n_comp == 2)
+        pairs_f64_kernel<false, 2><<<grid, 256, sizeof(F64Smem<2>), st>>>(s, ph, scale, a, partials, n_tiles, r);
+    else if (s.interaction > 0)
+        pairs_f64_kernel<true, 4><<<grid, 256, sizeof(F64Smem<4>), st>>>(s, ph, scale, a, partials, n_tiles, r);
     else
-        pairs_f64_kernel<false><<<grid, 256, smem, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, a,
-                                                         partials, n_tiles, r);
+        pairs_f64_kernel<false, 4><<<grid, 256, sizeof(F64Smem<4>), st>>>(s, ph, scale, a, partials, n_tiles, r);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // C ABI of the library (include/mcmp2.h): context, caller-owned workspace,
 // system loading with the host-side folding of the spinor coefficients, and
 // the orchestration of sampling, integrand and statistics on one stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -266,8 +267,15 @@ int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, siz
     return MCMP2_OK;
 }
 
-int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir, const double *C,
-                      const double *eps)
+}  // extern "C"
+
+namespace {
+
+// Loads a system whose coefficients C have 4 n_L rows (L-alpha, L-beta,
+// S-alpha, S-beta); n_comp = 2 marks a two-component system (C's small rows
+// are zero and the step evaluates 2 x 2 blocks).
+int load_system_impl(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir, const double *C, const double *eps,
+                     int n_comp)
 {
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->bound) return ctx->fail(MCMP2_ENOTLOADED, "no workspace bound");
@@ -412,6 +420,7 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     S.WL = ctx->at<double>(L.WL);
     S.WS = ctx->at<double>(L.WS);
     S.interaction = ctx->interaction;
+    S.n_comp = n_comp;
 
     uint64_t h = 1469598103934665603ull;
     h = fnv1a(h, b->centres, sizeof(double) * 3 * b->n_centres);
@@ -422,6 +431,7 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
     h = fnv1a(h, b->shell_coef, sizeof(double) * b->n_shells);
     h = fnv1a(h, C, sizeof(double) * 2 * 4 * (size_t)nl * no);
     h = fnv1a(h, eps, sizeof(double) * no);
+    h = fnv1a(h, &n_comp, sizeof(n_comp));
     // Cumulative masses of the weight function's Gaussians, for drawing initial positions.
     {
         std::vector<double> cdf(2 * (size_t)b->n_centres);
@@ -451,6 +461,36 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir
         }
     }
     return MCMP2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir, const double *C,
+                      const double *eps)
+{
+    return load_system_impl(ctx, b, n_occ, n_vir, C, eps, 4);
+}
+
+int mcmp2_load_system_2c(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir, const double *C2,
+                         const double *eps)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (ctx->precision != MCMP2_FP64)
+        return ctx->fail(MCMP2_EUNSUPPORTED, "two-component systems run in the FP64 form only");
+    if (ctx->interaction != MCMP2_COULOMB)
+        return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt / Breit terms need the small components");
+    if (!ctx->bound) return ctx->fail(MCMP2_ENOTLOADED, "no workspace bound");
+    if (!C2) return ctx->fail(MCMP2_EINVAL, "null pointer in system");
+    const size_t nl = (size_t)ctx->dims.n_functions, no = (size_t)n_occ + n_vir;
+    if (n_occ != ctx->dims.n_occ || n_vir != ctx->dims.n_vir)
+        return ctx->fail(MCMP2_EINVAL, "system sizes do not match the bound dims");
+    // Rows alpha, beta of the two-component spinors become the large rows of a
+    // four-component coefficient matrix whose small rows are zero.
+    std::vector<double> C4(4 * nl * no * 2, 0.0);
+    std::copy(C2, C2 + 2 * nl * no * 2, C4.begin());
+    return load_system_impl(ctx, b, n_occ, n_vir, C4.data(), eps, 2);
 }
 
 }  // extern "C"
@@ -708,6 +748,7 @@ int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double
     if (ctx->precision != MCMP2_FP64) return ctx->fail(MCMP2_EUNSUPPORTED, "the adjoint runs in the FP64 form");
     if (ctx->interaction != MCMP2_COULOMB)
         return ctx->fail(MCMP2_EUNSUPPORTED, "the adjoint covers the Coulomb interaction");
+    if (ctx->sys.n_comp != 4) return ctx->fail(MCMP2_EUNSUPPORTED, "the adjoint covers four-component systems");
     if (n < 1 || !r_host || !tau_host || !d_eps_host || !d_C_host) return ctx->fail(MCMP2_EINVAL, "bad backward arguments");
     const int m = ctx->dims.m, nt = ctx->dims.n_tau;
     if (!all_finite(r_host, (size_t)n * m * 6)) return ctx->fail(MCMP2_ENONFINITE, "non-finite position");
@@ -868,6 +909,8 @@ int mcmp2_set_interaction(mcmp2_ctx *ctx, int interaction)
         return ctx->fail(MCMP2_EINVAL, "unknown interaction");
     if (interaction != MCMP2_COULOMB && ctx->precision != MCMP2_FP64)
         return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt and Breit terms run in the FP64 form");
+    if (interaction != MCMP2_COULOMB && ctx->loaded && ctx->sys.n_comp == 2)
+        return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt / Breit terms need the small components");
     ctx->interaction = interaction;
     ctx->sys.interaction = interaction;
     ctx->drop_graph();  // the captured step holds the system by value

@@ -67,6 +67,7 @@ class System:
     C: np.ndarray  # [4 n_L, n_orb] complex128, occupied columns first
     eps: np.ndarray  # [n_orb] float64
     weight: np.ndarray  # [n_c, 4] float64: c1, zeta1, c2, zeta2
+    n_comp: int = 4  # 2: two-component spinors (alpha, beta rows only; the small rows of C are zero)
 
     @property
     def n_l(self) -> int:
@@ -81,7 +82,7 @@ class System:
         for a in (self.centres, self.shell_centre, self.shell_l, self.shell_alpha,
                   self.shell_coef, self.C, self.eps, self.weight):
             h.update(np.ascontiguousarray(a).tobytes())
-        h.update(f"{self.n_occ},{self.n_vir}".encode())
+        h.update(f"{self.n_occ},{self.n_vir},{self.n_comp}".encode())
         return h.hexdigest()[:16]
 
 
@@ -262,7 +263,7 @@ _SOFT_H = [(0, 0.08, 2.5, 3)]                                        # 3
 
 
 def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = False,
-                small_scale: float | None = None) -> System:
+                small_scale: float | None = None, two_component: bool = False) -> System:
     """Draw one of the synthetic systems.
 
     config: "tiny" (Z=30 + Z=1, n_L = 20, 4 occ / 16 vir),
@@ -274,7 +275,10 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     orthonormalisation (default 1/(2c), the kinetic-balance size); a test
     system with small_scale = 1 has small components of order one, so terms
     that couple large and small components (the Gaunt/Breit interaction) are
-    of the size of the Coulomb ones."""
+    of the size of the Coulomb ones.
+    two_component: two-component spinors (alpha, beta) over the large basis
+    only, orthonormal in S_LL; C keeps 4 n_L rows with the small rows zero and
+    the system is marked n_comp = 2."""
     rng = np.random.default_rng(seed)
     charges, centres = _geometry(config, n_units)
     shells = []
@@ -313,6 +317,8 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
 
     half = rng.standard_normal((4 * n_l, n_orb // 2)) + 1j * rng.standard_normal((4 * n_l, n_orb // 2))
     half[2 * n_l:] *= (1.0 / (2.0 * SPEED_OF_LIGHT)) if small_scale is None else float(small_scale)
+    if two_component:
+        half[2 * n_l:] = 0.0
     # Per-entry spread: each basis function counts with unit norm, and an
     # orbital of energy eps draws mostly on functions whose exponent matches
     # its spatial extent (alpha ~ 0.57 |eps|, the best single Gaussian for a
@@ -336,10 +342,13 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
         name += "-soft"
     if small_scale is not None:
         name += f"-small{small_scale:g}"
+    if two_component:
+        name += "-2c"
     return System(name=name, centres=np.ascontiguousarray(centres, dtype=np.float64),
                   charges=np.array(charges, dtype=np.int32), shell_centre=shell_centre,
                   shell_l=shell_l, shell_alpha=shell_alpha, shell_coef=shell_coef,
-                  n_occ=n_occ, n_vir=n_vir, C=np.ascontiguousarray(C), eps=eps, weight=weight)
+                  n_occ=n_occ, n_vir=n_vir, C=np.ascontiguousarray(C), eps=eps, weight=weight,
+                  n_comp=2 if two_component else 4)
 
 
 def nonrelativistic_variant(system: System, seed: int = 7) -> System:
