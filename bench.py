@@ -41,7 +41,7 @@ TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 # DRAM bytes (read + write) of one contraction launch at m = 1024, 4 tau, from
 # the ncu captures summarised in profiles/pairs_mixed_{bf16x3,tf32}_medium_m1024.md
 # (the kernels as they stand); None for other sizes.
-PAIRS_TRAFFIC_BYTES = {"mixed": 138.1e6, "tf32": 138.3e6}
+PAIRS_TRAFFIC_BYTES = {"mixed": 138.0e6, "tf32": 137.8e6}
 
 
 def flops_per_sample(n_occ, n_vir, n_comp=4):
