@@ -159,8 +159,11 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n
  * [2 n_L][n_occ + n_vir] row-major, rows alpha block then beta block; the other
  * arguments and checks as in mcmp2_load_system.  The result equals
  * mcmp2_load_system with these rows as L-alpha, L-beta and zero small rows.
- * FP64 contexts with the Coulomb interaction only (MCMP2_EUNSUPPORTED
- * otherwise, and from mcmp2_set_interaction and mcmp2_backward afterwards). */
+ * All three precisions; the tensor-core forms contract 32 x 32-pair tiles of
+ * 2x2 blocks (mcmp2_debug_partials then reports tile_pairs = 32).  The Coulomb
+ * interaction only (MCMP2_EUNSUPPORTED otherwise, also from
+ * mcmp2_set_interaction afterwards); mcmp2_backward covers four-component
+ * systems only. */
 int mcmp2_load_system_2c(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n_vir,
                          const double *C2_host, const double *eps_host);
 

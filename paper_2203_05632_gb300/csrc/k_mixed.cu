@@ -130,11 +130,12 @@ struct SpinorArgs {
     int *abort_flag;
     int P, nl, n_mt, n_kb, n_kb_occ, n_occ, n_vir, n_orb, n_tau, rows, k_occ_pad, k_vir_pad;
     int tf32;  // chunk = 16 re (TF32) + 16 im (TF32) instead of re_hi, re_lo, im_hi, im_lo (BF16)
+    int ncomp; // spinor components: 4, or 2 (two-component systems: large components only, rows 2x + c)
 };
 
-__device__ __forceinline__ void sp_tile(int tile, int n_kb, int &mt, int &c4, int &kb)
+__device__ __forceinline__ void sp_tile(int tile, int n_kb, int ncomp, int &mt, int &c4, int &kb)
 {
-    const int per = 4 * n_kb;
+    const int per = ncomp * n_kb;
     mt = tile / per;
     const int nt = tile - mt * per;
     c4 = nt / n_kb;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
     uint64_t *tempty = tfull + 2;         // [2]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = args.n_mt * 4 * args.n_kb;
+    const int n_tiles = args.n_mt * args.ncomp * args.n_kb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < SP_STAGES; ++s) {
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 int mt, c4, kb;
-                sp_tile(tile, args.n_kb, mt, c4, kb);
+                sp_tile(tile, args.n_kb, args.ncomp, mt, c4, kb);
                 const bool grad = c4 >= 2;
                 const CUtensorMap *mp = &maps.m[grad ? 4 : 0];
                 const int K = grad ? 3 * args.nl : args.nl;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             const uint64_t bh0 = sdesc_sw64(base0 + 2 * TILE_BYTES), bl0 = sdesc_sw64(base0 + 3 * TILE_BYTES);
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 int mt, c4, kb;
-                sp_tile(tile, args.n_kb, mt, c4, kb);
+                sp_tile(tile, args.n_kb, args.ncomp, mt, c4, kb);
                 const int K = c4 >= 2 ? 3 * args.nl : args.nl;
                 if (!mbar_wait_fast(&tempty[buf], tphase[buf] ^ 1u, args.abort_flag, 12, TIMEOUT_NS)) {
                     ok = false;
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         uint32_t ephase[2] = {0, 0};
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
             int mt, c4, kb;
-            sp_tile(tile, args.n_kb, mt, c4, kb);
+            sp_tile(tile, args.n_kb, args.ncomp, mt, c4, kb);
             const bool got = mbar_wait(&tfull[buf], ephase[buf], args.abort_flag, 14, TIMEOUT_NS);
             if (bar_any<1, 32 * SP_EPI_WARPS>(!got)) break;  // also: every epilogue warp is done with the previous scales
             ephase[buf] ^= 1u;
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                     const int x = mt * 128 + 32 * quarter + row;
                     if (x < args.P) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * piece);
-                        __nv_bfloat16 *dst = planes + (size_t)t * time_elems + (size_t)(4 * x + c4) * (4 * kpad) +
+                        __nv_bfloat16 *dst = planes + (size_t)t * time_elems + (size_t)(args.ncomp * x + c4) * (4 * kpad) +
                                              kl * 256 + jh * 128 + 8 * piece;
                         *reinterpret_cast<uint4 *>(dst) = v;
                     }
@@ -407,7 +408,7 @@ constexpr int PR_GM_BYTES = PR_GM_PACKED ? 16 * 3 * 128 * 8 : 16 * 2 * 128 * 16;
 constexpr int PR_GM_OFF = PR_STAGES * PR_STAGE_BYTES;
 constexpr int PR_BARS_OFF = PR_GM_OFF + PR_GROUPS * PR_GM_BYTES;
 constexpr int PR_RED_OFF = PR_BARS_OFF + 192;      // barriers + tensor-memory slot
-constexpr int PR_SMEM = PR_RED_OFF + PR_GROUPS * 32 * 8 + 1024;
+constexpr int PR_SMEM = PR_RED_OFF + PR_GROUPS * 64 * 8 + 1024;
 static_assert(PR_SMEM <= 232448, "contraction kernel exceeds the shared memory of one CTA");
 static_assert((2 * PR_STAGES + 4 * PR_GROUPS) * 8 + 4 <= 192, "barrier block too small");
 
@@ -484,7 +485,140 @@ __device__ __forceinline__ void group_sync(int g)
         bar_sync<2, 32 * PR_GROUP_WARPS>();
 }
 
-template <bool TF32>
+// Trace epilogue of a two-component tile (NC = 2): rows 4p + 2e + c of 32
+// p-pairs, columns 4q + 2e' + d of 32 q-pairs, so the four lanes (e, c) of a
+// pair hold its rows.  Same hand-offs as the four-component epilogue: unload
+// the like-electron blocks G-(ep, eq) (2 x 2) to shared memory as 24-bit
+// floats, then trace against G+ once it is in the same columns.
+__device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned char *smem, uint32_t tmem,
+                                                  int warp, int lane, int n_items, uint64_t *mfull,
+                                                  uint64_t *munl, uint64_t *pfull, uint64_t *pfree)
+{
+    const int ew = warp - 2;
+    const int g = ew / PR_GROUP_WARPS;
+    const int gw = ew - g * PR_GROUP_WARPS;
+    const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+    const int qhalf = gw >> 2;     // q-pairs 16*qhalf .. +15 of the tile
+    const int row = 32 * quarter + lane;
+    const int p_local = row >> 2, e = (row >> 1) & 1, c = lane & 1;
+    const int gbase = lane & ~3;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + 256u * g;
+    uint32_t *gw32 = reinterpret_cast<uint32_t *>(smem + PR_GM_OFF + g * PR_GM_BYTES);  // [32 q][3][128 rows]
+    double *red = reinterpret_cast<double *>(smem + PR_RED_OFF) + 64 * g;
+    uint32_t ph = 0;
+    for (int item = blockIdx.x + g * gridDim.x; item < n_items; item += PR_GROUPS * gridDim.x) {
+        const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
+        int bp, bq;
+        pair_tile(tile, args.nb, bp, bq);
+        // (1) G-(xe, ye) row c: entries d = 0, 1 (re, im), packed into three words per q.
+        const bool got_m = mbar_wait(&mfull[g], ph, args.abort_flag, 4, args.timeout_ns);
+        if (group_any(g, !got_m)) break;
+        fence_after();
+#pragma unroll 1
+        for (int qb = 0; qb < 4; ++qb) {
+            const int q0 = 16 * qhalf + 4 * qb;  // four q-pairs per tensor-memory load
+            float vr[16], vi[16];
+            tmem_ld<16>(lane_addr + 4u * q0, vr);
+            tmem_ld<16>(lane_addr + 128u + 4u * q0, vi);
+            tmem_wait_ld();
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const float o0r = e ? vr[4 * qq + 2] : vr[4 * qq], o0i = e ? vi[4 * qq + 2] : vi[4 * qq];
+                const float o1r = e ? vr[4 * qq + 3] : vr[4 * qq + 1], o1i = e ? vi[4 * qq + 3] : vi[4 * qq + 1];
+                const uint3 u = pack24(o0r, o0i, o1r, o1i);
+                const int q = q0 + qq;
+                gw32[(3 * q + 0) * 128 + row] = u.x;
+                gw32[(3 * q + 1) * 128 + row] = u.y;
+                gw32[(3 * q + 2) * 128 + row] = u.z;
+            }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&munl[g]);
+        // (2) traces once G+ is in the same columns.
+        const bool got_p = mbar_wait(&pfull[g], ph, args.abort_flag, 6, args.timeout_ns);
+        if (group_any(g, !got_p)) break;
+        ph ^= 1u;
+        fence_after();
+        const int p = bp * 32 + p_local;
+        const int q_lane = bq * 32 + lane;  // a_q of the tile's 32 q-pairs, one per lane
+        const double a_lane = q_lane < args.m ? args.a[q_lane] : 0.0;
+        double acc = 0.0;
+#pragma unroll 1
+        for (int qb = 0; qb < 4; ++qb) {
+            const int q0 = 16 * qhalf + 4 * qb;
+            float gpr[16], gpi[16];
+            tmem_ld<16>(lane_addr + 4u * q0, gpr);
+            tmem_ld<16>(lane_addr + 128u + 4u * q0, gpi);
+            tmem_wait_ld();
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                // Row c of G-(xe, ye) [own], G+(xe, ye) [dia], G+(xe, y(1-e)) [off].
+                const int ql = q0 + qq;
+                float own_r[2], own_i[2];
+                unpack24(gw32[(3 * ql + 0) * 128 + row], gw32[(3 * ql + 1) * 128 + row],
+                         gw32[(3 * ql + 2) * 128 + row], own_r[0], own_i[0], own_r[1], own_i[1]);
+                float dia_r[2], dia_i[2], off_r[2], off_i[2];
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    const int i0 = 4 * qq + d, i1 = 4 * qq + 2 + d;
+                    dia_r[d] = e ? gpr[i1] : gpr[i0];
+                    dia_i[d] = e ? gpi[i1] : gpi[i0];
+                    off_r[d] = e ? gpr[i0] : gpr[i1];
+                    off_i[d] = e ? gpi[i0] : gpi[i1];
+                }
+                // Direct: T_e = sum_cd conj(G-_cd) G+_cd over the like-electron block.
+                float tr = 0.f, ti = 0.f;
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    tr += own_r[d] * dia_r[d] + own_i[d] * dia_i[d];
+                    ti += own_r[d] * dia_i[d] - own_i[d] * dia_r[d];
+                }
+                tr += __shfl_xor_sync(0xffffffffu, tr, 1);
+                ti += __shfl_xor_sync(0xffffffffu, ti, 1);
+                const float ur = __shfl_xor_sync(0xffffffffu, tr, 2);
+                const float ui = __shfl_xor_sync(0xffffffffu, ti, 2);
+                const float direct_re = tr * ur - ti * ui;
+                // Exchange: sum_{c,c''} U_{cc''} V_{c''c} with U = G+(1p,2q) G-(2p,2q)^dag and
+                // V = G+(2p,1q) G-(1p,1q)^dag: lane (0, c) takes c'' = c, lane (1, c'') takes c = 1 - c'',
+                // each pairing its rows with those of the other electron's lane.
+                const int src = gbase + (e == 0 ? 2 + c : 1 - c);
+                float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    const float rg_r = __shfl_sync(0xffffffffu, own_r[d], src);
+                    const float rg_i = __shfl_sync(0xffffffffu, own_i[d], src);
+                    const float ro_r = __shfl_sync(0xffffffffu, off_r[d], src);
+                    const float ro_i = __shfl_sync(0xffffffffu, off_i[d], src);
+                    a1r += off_r[d] * rg_r + off_i[d] * rg_i;
+                    a1i += off_i[d] * rg_r - off_r[d] * rg_i;
+                    a2r += ro_r * own_r[d] + ro_i * own_i[d];
+                    a2i += ro_i * own_r[d] - ro_r * own_i[d];
+                }
+                float xr = a1r * a2r - a1i * a2i;
+                xr += __shfl_xor_sync(0xffffffffu, xr, 1);
+                xr += __shfl_xor_sync(0xffffffffu, xr, 2);
+                const int q = bq * 32 + ql;
+                const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
+                const bool valid = p < args.m && q < args.m && (bp < bq || p_local < ql);
+                if (valid) acc += (double)(-0.5f * (direct_re - xr)) * a_q;
+            }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pfree[g]);
+        if ((lane & 3) == 0) red[32 * qhalf + 8 * quarter + (lane >> 2)] = (p < args.m) ? acc * args.a[p] : 0.0;
+        group_sync(g);
+        if (gw == 0 && lane == 0) {
+            double sum = 0.0;
+            for (int j = 0; j < 64; ++j) sum += red[j];
+            args.partials[(size_t)t * args.n_tiles + tile] = sum * args.inv_lambda;
+        }
+        group_sync(g);
+    }
+}
+
+template <bool TF32, int NC>
 __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid_constant__ PairMaps maps,
                                                                     const PairArgs args)
 {
@@ -656,6 +790,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             umma_commit(&empty[stage]);
             mbar_drain(&empty[stage], phase, args.timeout_ns);
         }
+    } else if constexpr (NC == 2) {
+        pairs_epilogue_2c(args, smem, tmem, warp, lane, n_items, mfull, munl, pfull, pfree);
     } else {
         // ---------------- epilogue: two groups of 8 warps, alternate items ----------------
         const int ew = warp - 2;
@@ -987,11 +1123,14 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
             (rc = encode(plan.maps_spinor[7], ws + L.WTS_lo, 2, wsd, ss_, err)))
             return rc;
     }
-    // Contraction: operand rows [n_tau][rows][4 k_pad] as a 3-D tensor (chunk x plane x orbital, row, tau).
+    // Contraction: operand rows [n_tau][rows][4 k_pad] as a 3-D tensor (chunk x plane x orbital, row, tau);
+    // a two-component system fills the first 4m of the 8m rows of each time.
+    plan.ncomp = s.n_comp == 2 ? 2 : 4;
+    const int rows_used = 2 * plan.ncomp * s.m;
     {
-        const cuuint64_t dO[3] = {(cuuint64_t)4 * L.k_occ_pad, (cuuint64_t)L.rows, (cuuint64_t)L.n_tau};
+        const cuuint64_t dO[3] = {(cuuint64_t)4 * L.k_occ_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
         const cuuint64_t sO[2] = {(cuuint64_t)L.k_occ_pad * 8, (cuuint64_t)L.rows * L.k_occ_pad * 8};
-        const cuuint64_t dV[3] = {(cuuint64_t)4 * L.k_vir_pad, (cuuint64_t)L.rows, (cuuint64_t)L.n_tau};
+        const cuuint64_t dV[3] = {(cuuint64_t)4 * L.k_vir_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
         const cuuint64_t sV[2] = {(cuuint64_t)L.k_vir_pad * 8, (cuuint64_t)L.rows * L.k_vir_pad * 8};
         if ((rc = encode(plan.maps_pairs[0], ws + L.occ_planes, 3, dO, sO, err, 4 * PR_BK, CU_TENSOR_MAP_SWIZZLE_128B)) ||
             (rc = encode(plan.maps_pairs[1], ws + L.vir_planes, 3, dV, sV, err, 4 * PR_BK, CU_TENSOR_MAP_SWIZZLE_128B)))
@@ -999,9 +1138,13 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
     }
     if (cudaFuncSetAttribute(spinor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(pairs_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
+        cudaFuncSetAttribute(pairs_mixed_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(pairs_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
+        cudaFuncSetAttribute(pairs_mixed_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
             cudaSuccess) {
         err = "cannot reserve shared memory for the tensor-core kernels";
         return MCMP2_ECUDA;
@@ -1032,14 +1175,15 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     std::memcpy(&smaps, plan.maps_spinor, sizeof(smaps));
     const int n_mt = (L.P + 127) / 128;
     SpinorArgs sa{scale, bf(L.occ_planes), bf(L.vir_planes), flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ,
-                  s.n_occ, s.n_vir, s.n_orb, s.n_tau, L.rows, L.k_occ_pad, L.k_vir_pad, plan.tf32 ? 1 : 0};
-    const int sp_tiles = n_mt * 4 * L.n_kb;
+                  s.n_occ, s.n_vir, s.n_orb, s.n_tau, L.rows, L.k_occ_pad, L.k_vir_pad, plan.tf32 ? 1 : 0,
+                  plan.ncomp};
+    const int sp_tiles = n_mt * plan.ncomp * L.n_kb;
     spinor_mixed_kernel<<<sp_tiles < sms ? sp_tiles : sms, SP_THREADS, SP_SMEM, st>>>(smaps, sa);
 
     PairMaps pmaps;
     std::memcpy(&pmaps.occ, plan.maps_pairs[0], sizeof(CUtensorMap));
     std::memcpy(&pmaps.vir, plan.maps_pairs[1], sizeof(CUtensorMap));
-    const int nb = pair_blocks(s.m, 16);
+    const int nb = pair_blocks(s.m, plan.ncomp == 2 ? TILE_PAIRS_MIXED_2C : TILE_PAIRS_MIXED);
     const int n_tiles = nb * (nb + 1) / 2;
     PairArgs pa{a, partials, flag, s.m, n_tiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda, TIMEOUT_NS, 0};
     if (plan.withhold_once_ns) {
@@ -1049,10 +1193,17 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     }
     const int items = n_tiles * s.n_tau;
     if (ev) record_event(ev[0], st);
-    if (plan.tf32)
-        pairs_mixed_kernel<true><<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
-    else
-        pairs_mixed_kernel<false><<<items < sms ? items : sms, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+    const int grid = items < sms ? items : sms;
+    if (plan.ncomp == 2) {
+        if (plan.tf32)
+            pairs_mixed_kernel<true, 2><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+        else
+            pairs_mixed_kernel<false, 2><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+    } else if (plan.tf32) {
+        pairs_mixed_kernel<true, 4><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+    } else {
+        pairs_mixed_kernel<false, 4><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
+    }
     if (ev) record_event(ev[1], st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

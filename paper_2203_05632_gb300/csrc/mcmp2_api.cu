@@ -421,6 +421,10 @@ int load_system_impl(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir,
     S.WS = ctx->at<double>(L.WS);
     S.interaction = ctx->interaction;
     S.n_comp = n_comp;
+    if (ctx->precision != MCMP2_FP64) {  // a two-component tile holds 32 pairs (4 operand rows each)
+        ctx->L.tile_pairs = n_comp == 2 ? TILE_PAIRS_MIXED_2C : TILE_PAIRS_MIXED;
+        ctx->L.n_tiles = n_tiles_for(d.m, ctx->L.tile_pairs);
+    }
 
     uint64_t h = 1469598103934665603ull;
     h = fnv1a(h, b->centres, sizeof(double) * 3 * b->n_centres);
@@ -477,8 +481,6 @@ int mcmp2_load_system_2c(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_
                          const double *eps)
 {
     if (!ctx) return MCMP2_EINVAL;
-    if (ctx->precision != MCMP2_FP64)
-        return ctx->fail(MCMP2_EUNSUPPORTED, "two-component systems run in the FP64 form only");
     if (ctx->interaction != MCMP2_COULOMB)
         return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt / Breit terms need the small components");
     if (!ctx->bound) return ctx->fail(MCMP2_ENOTLOADED, "no workspace bound");

@@ -24,6 +24,7 @@ struct MixedLayout {
 struct MixedPlan {
     bool ready = false;
     bool tf32 = false;  // propagator operands as TF32 (re, im) instead of split BF16 (re hi/lo, im hi/lo)
+    int ncomp = 4;      // spinor components of the loaded system (2: 32-pair tiles of 2 x 2 blocks)
     unsigned long long withhold_once_ns = 0;  // test hook for the bounded-wait path (see mcmp2_test_stall_next)
     alignas(64) unsigned char maps_spinor[8][128];
     alignas(64) unsigned char maps_pairs[2][128];

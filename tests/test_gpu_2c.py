@@ -1,10 +1,11 @@
-"""The two-component variant (mcmp2_load_system_2c, FP64 form) against the oracle.
+"""The two-component variant (mcmp2_load_system_2c) against the oracle, in all three forms.
 
 Two-spinors (alpha, beta) over the large basis: G- and G+ are 2 x 2 blocks in the
 trace form of Eq. MCMP2 (Sec. II names two-component Hamiltonians as covered by
 the same algorithm).  Parity bar as for the four-component FP64 form: 1e-10
-relative per step estimate, relative to max(|I'_n|, 1e-3 <|f|>); the oracle
-evaluates the same estimator with the small-component rows of C zero.
+relative per step estimate, relative to max(|I'_n|, 1e-3 <|f|>); the tensor-core
+forms (32 x 32-pair tiles) are held to the bounds of their four-component tests.
+The oracle evaluates the same estimator with the small-component rows of C zero.
 """
 import dataclasses
 
@@ -17,6 +18,8 @@ import synthetic
 from oracle import mp2
 
 from test_gpu_fp64 import _check_steps, _tile_index, _tile_pairs
+from test_gpu_mixed import _ok as _mixed_ok
+from test_gpu_tf32 import _bound as _tf32_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -120,9 +123,75 @@ def test_two_component_long_walk_matches_deterministic_energy():
     assert res["error"] < 0.05 * abs(e2)
 
 
+@pytest.mark.parametrize("prec", [pkg.MCMP2_MIXED, pkg.MCMP2_TF32])
+@pytest.mark.parametrize("m,n_tau", [(16, 1), (13, 3), (2, 1), (33, 2), (70, 1)])
+def test_two_component_tensor_forms_match_oracle_tiny(tiny2c, tiny2c_oracle, prec, m, n_tau):
+    """32 x 32-pair tiles of 2 x 2 blocks (ragged: m = 33, 70 span two and three
+    tile rows) within the bounds of the four-component tensor forms."""
+    n = 2
+    r = synthetic.walker_positions(tiny2c.centres, n, m, seed=500 + m)
+    tau = synthetic.imaginary_times(tiny2c_oracle.lam(), n, n_tau, seed=19 + m)
+    ctx = pkg.Context(tiny2c, m, n_tau, prec)
+    got = ctx.eval_fixed(r, tau)
+    want, absmean = tiny2c_oracle.eval_steps(r, tau, with_abs=True)
+    if prec == pkg.MCMP2_MIXED:
+        assert np.all(_mixed_ok(got, want, absmean)), (got, want)
+    else:
+        for k in range(n):
+            bound = _tf32_bound(tiny2c_oracle, tiny2c, r[k], tau[k])
+            assert abs(got[k] - want[k]) <= bound, (k, got[k], want[k], bound)
+
+
+def test_two_component_mixed_full_size_sampled_tiles(medium2c, medium2c_oracle):
+    m, n_tau = 1024, 4
+    r = synthetic.walker_positions(medium2c.centres, 1, m, seed=71)
+    tau = synthetic.imaginary_times(medium2c_oracle.lam(), 1, n_tau, seed=72)
+    ctx = pkg.Context(medium2c, m, n_tau, pkg.MCMP2_MIXED)
+    step = ctx.eval_fixed(r, tau)[0]
+    partials, tp = ctx.debug_partials()
+    assert tp == 32
+    nb = (m + tp - 1) // tp
+    assert partials.shape[1] == nb * (nb + 1) // 2
+    assert step == pytest.approx(partials.sum() / (m * (m - 1) / 2) / n_tau, rel=1e-12)
+    for bp, bq in [(0, 0), (0, 1), (5, 20), (nb - 1, nb - 1), (15, nb - 1)]:
+        ps, qs = _tile_pairs(bp, bq, tp, m)
+        vals = medium2c_oracle.eval_pairs(r[0], tau[0], ps, qs)
+        want = vals.sum(axis=0)
+        got = partials[:, _tile_index(bp, bq, nb)]
+        assert np.all(_mixed_ok(got, want, np.abs(vals).sum(axis=0))), (bp, bq, got, want)
+
+
+@pytest.mark.parametrize("prec", [pkg.MCMP2_MIXED, pkg.MCMP2_TF32])
+def test_two_component_tensor_forms_agree_with_fp64_within_a_fifth_of_sigma(medium2c, prec):
+    m, n_tau, seed, n = 96, 2, 909, 400
+    r0 = synthetic.walker_positions(medium2c.centres, 1, m, seed=4)[0]
+    per = {}
+    for pr in (pkg.MCMP2_FP64, prec):
+        ctx = pkg.Context(medium2c, m, n_tau, pr)
+        ctx.set_walkers(r0, seed, 100)
+        per[pr] = np.array([ctx.run_steps(1, seed)["last_step"] for _ in range(n)])
+        ctx.close()
+    d = per[prec] - per[pkg.MCMP2_FP64]
+    _, _, sb, nb = oracle.blocking(per[pkg.MCMP2_FP64])
+    assert nb == 4
+    assert abs(d.mean()) < 0.2 * sb, (d.mean(), sb)
+
+
+def test_two_component_mixed_long_walk_matches_deterministic_energy():
+    soft2c = synthetic.make_system("tiny", soft=True, two_component=True)
+    e2 = mp2.mp2_energy(soft2c, mp2.spinor_eri(oracle.Oracle(soft2c)))
+    ctx = pkg.Context(soft2c, 64, 2, pkg.MCMP2_MIXED)
+    ctx.set_walkers(synthetic.walker_positions(soft2c.centres, 1, 64, seed=11)[0], 4242, 500)
+    res = ctx.run_steps(20000, 4242)
+    z = (res["energy"] - e2) / res["error"]
+    print(f"soft tiny 2c, split BF16: E = {res['energy']:.6f} +- {res['error']:.6f}, E2 = {e2:.6f}, z = {z:.2f}")
+    assert abs(z) < 3.0, (res["energy"], res["error"], e2)
+
+
 def test_two_component_guards(tiny2c):
+    mixed = pkg.Context(tiny2c, 8, 1, pkg.MCMP2_MIXED)
     with pytest.raises(pkg.McMp2Error) as e:
-        pkg.Context(tiny2c, 8, 1, pkg.MCMP2_MIXED)
+        mixed.set_interaction(pkg.MCMP2_GAUNT)
     assert e.value.code == pkg.MCMP2_EUNSUPPORTED
     ctx = pkg.Context(tiny2c, 8, 1, pkg.MCMP2_FP64)
     with pytest.raises(pkg.McMp2Error) as e:
