@@ -156,3 +156,43 @@ def test_mc_eps_gradient_matches_deterministic_mp2(tiny_soft, soft_oracle):
     z = (mc - exact) / np.maximum(err, 1e-12)
     assert np.max(np.abs(z)) < 5.0, (mc, exact, err)
     assert np.mean(z ** 2) < 4.0, z
+
+
+def test_adjoint_at_the_adjoint_configuration_size(adj_system):
+    """The adjoint workload's launch size (m = 512 walker pairs, one time per step):
+    orbital-energy and coefficient gradients against central differences."""
+    m, n_tau = 512, 1
+    r, tau = _samples(adj_system, _lam(adj_system), 2, m, n_tau, 17)
+    ctx = pkg.Context(adj_system, m, n_tau, pkg.MCMP2_FP64)
+    e0, d_eps, d_C = ctx.backward(r, tau)
+    assert e0 == pytest.approx(ctx.eval_fixed(r, tau).mean(), rel=1e-11)
+    eps0, C0 = adj_system.eps.copy(), adj_system.C.copy()
+    ks = _non_frontier(adj_system)
+    scale = np.abs(d_eps).max()
+    for k in (ks[1], ks[len(ks) // 2], ks[-2]):
+        e = []
+        for sgn in (1, -1):
+            eps = eps0.copy()
+            eps[k] += sgn * H
+            ctx.load(eps=eps)
+            e.append(ctx.eval_fixed(r, tau).mean())
+        fd = (e[0] - e[1]) / (2 * H)
+        assert abs(fd - d_eps[k]) <= REL_FD * max(abs(d_eps[k]), 1e-3 * scale), (k, fd, d_eps[k])
+    ctx.load(eps=eps0)
+    # A direction through every coefficient: the estimate is a polynomial of degree 8
+    # in C, so the O(h^2) truncation of one central difference reaches ~1e-5 here;
+    # Richardson's combination of steps h and h/2 cancels it (O(h^4)).
+    rng = np.random.default_rng(23)
+    D = rng.standard_normal(C0.shape) + 1j * rng.standard_normal(C0.shape)
+    D *= np.abs(C0).max() / np.abs(D).max()
+
+    def central(h):
+        e = []
+        for sgn in (1, -1):
+            ctx.load(C=C0 + sgn * h * D)
+            e.append(ctx.eval_fixed(r, tau).mean())
+        return (e[0] - e[1]) / (2 * h)
+
+    fd = (4.0 * central(H / 2) - central(H)) / 3.0
+    ad = float(np.real(np.sum(np.conj(d_C) * D)))
+    assert abs(fd - ad) <= REL_FD * max(abs(ad), 1e-12), (fd, ad)

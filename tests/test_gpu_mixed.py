@@ -153,3 +153,34 @@ def test_timing_mode_outside_graphs(tiny):
         ctx.eval_fixed(r, tau)
         prof = ctx.profile(0)
         assert prof["pair_launches"] == 2 and prof["pair_ms"] > 0.0
+
+
+@pytest.mark.parametrize("prec", [pkg.MCMP2_MIXED, pkg.MCMP2_TF32])
+def test_size_series_launch_sampled_tiles(prec):
+    """The size-series launch (m = 4096 walker pairs, 8 times; a two-unit cluster,
+    80 / 360 spinors): sampled 16 x 16 tiles against the oracle's pair values, in
+    the bound of each form (split BF16: the tolerance above; TF32: 8 u times the
+    tile's absolute expansion)."""
+    from test_gpu_tf32 import U_TF32, _abs_expansion_sum
+    system = synthetic.make_system("size", n_units=2)
+    orc = oracle.Oracle(system)
+    m, n_tau = 4096, 8
+    r = synthetic.walker_positions(system.centres, 1, m, seed=61)
+    tau = synthetic.imaginary_times(orc.lam(), 1, n_tau, seed=62)
+    ctx = pkg.Context(system, m, n_tau, prec)
+    step = ctx.eval_fixed(r, tau)[0]
+    partials, tp = ctx.debug_partials()
+    nb = (m + tp - 1) // tp
+    assert step == pytest.approx(partials.sum() / (m * (m - 1) / 2) / n_tau, rel=1e-12)
+    for bp, bq in [(0, 0), (3, 200), (nb - 1, nb - 1), (128, nb - 1)]:
+        ps, qs = _tile_pairs(bp, bq, tp, m)
+        vals = orc.eval_pairs(r[0], tau[0], ps, qs)
+        want = vals.sum(axis=0)
+        got = partials[:, sum(nb - b for b in range(bp)) + (bq - bp)]
+        if prec == pkg.MCMP2_MIXED:
+            assert np.all(_ok(got, want, np.abs(vals).sum(axis=0))), (bp, bq, got, want)
+        else:
+            pairs = list(zip(ps.tolist(), qs.tolist()))
+            for t in range(n_tau):
+                bound = 8.0 * U_TF32 * _abs_expansion_sum(orc, system, r[0], tau[0][t:t + 1], pairs)[0]
+                assert abs(got[t] - want[t]) <= bound, (bp, bq, t, got[t], want[t], bound)
