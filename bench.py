@@ -40,8 +40,8 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 CUDA-core FP64 (no FP64 tensor path on this 
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 # DRAM bytes (read + write) of one contraction launch at m = 1024, 4 tau, from
 # the ncu captures summarised in profiles/pairs_mixed_{bf16x3,tf32}_medium_m1024.md
-# (the kernels as they stand); None for other sizes.
-PAIRS_TRAFFIC_BYTES = {"mixed": 138.0e6, "tf32": 137.8e6}
+# (the kernels as they stand; None where no capture of the current kernel exists).
+PAIRS_TRAFFIC_BYTES = {"mixed": None, "tf32": None}
 
 
 def flops_per_sample(n_occ, n_vir, n_comp=4):

@@ -127,6 +127,8 @@ struct SpinorArgs {
     const float *scale;   // [n_tau][n_orb]
     __nv_bfloat16 *occ;   // [n_tau][rows][k_occ_pad / 16][128 B]
     __nv_bfloat16 *vir;   // [n_tau][rows][k_vir_pad / 16][128 B]
+    __nv_bfloat16 *iocc;  // i X in the same layout (planes -im, re)
+    __nv_bfloat16 *ivir;
     int *abort_flag;
     int P, nl, n_mt, n_kb, n_kb_occ, n_occ, n_vir, n_orb, n_tau, rows, k_occ_pad, k_vir_pad;
     int tf32;  // chunk = 16 re (TF32) + 16 im (TF32) instead of re_hi, re_lo, im_hi, im_lo (BF16)
@@ -289,6 +291,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             const int k_first = (occ ? 0 : args.n_occ) + kl * 64;  // absolute index of the block's first orbital
             const int k_end = occ ? args.n_occ : args.n_orb;       // one past the region's last orbital
             __nv_bfloat16 *planes = occ ? args.occ : args.vir;
+            __nv_bfloat16 *iplanes = occ ? args.iocc : args.ivir;
+            const uint32_t neg = args.tf32 ? 0x80000000u : 0x80008000u;  // sign bits of the packed values
             const size_t time_elems = (size_t)args.rows * 4 * kpad;  // one time's operand rows
             for (int i = threadIdx.x - 64; i < 64 * args.n_tau; i += 32 * SP_EPI_WARPS) {
                 const int t = i >> 6, k = k_first + (i & 63);
@@ -342,16 +346,27 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                     }
                 }
                 __syncwarp();
+                // Each row's 256 bytes (two chunks), 16 per lane, to X; and to iX = i X, whose
+                // chunk holds -im then re: piece p of a chunk comes from piece p ^ 4, negated
+                // in the first half.
                 const int half = lane >> 4, piece = lane & 15;
+                const int ipiece = (piece & 8) | ((piece & 7) ^ 4);
+                const uint32_t flip = (piece & 4) ? 0u : neg;
 #pragma unroll 4
                 for (int it = 0; it < 16; ++it) {
                     const int row = 2 * it + half;
                     const int x = mt * 128 + 32 * quarter + row;
                     if (x < args.P) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * piece);
-                        __nv_bfloat16 *dst = planes + (size_t)t * time_elems + (size_t)(args.ncomp * x + c4) * (4 * kpad) +
-                                             kl * 256 + jh * 128 + 8 * piece;
-                        *reinterpret_cast<uint4 *>(dst) = v;
+                        uint4 w = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * ipiece);
+                        w.x ^= flip;
+                        w.y ^= flip;
+                        w.z ^= flip;
+                        w.w ^= flip;
+                        const size_t off = (size_t)t * time_elems + (size_t)(args.ncomp * x + c4) * (4 * kpad) +
+                                           kl * 256 + jh * 128 + 8 * piece;
+                        *reinterpret_cast<uint4 *>(planes + off) = v;
+                        *reinterpret_cast<uint4 *>(iplanes + off) = w;
                     }
                 }
                 __syncwarp();
@@ -373,69 +388,95 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
 // ===========================================================================
 // 3. Pair-of-pairs contraction with the trace epilogue
 // ===========================================================================
-// Operand rows: one row per (position x, component c), row 4x + c, holding
-// for each 16-orbital chunk the four split planes re_hi, re_lo, im_hi, im_lo
-// side by side (128 B), so one 128-byte-swizzled TMA box of 128 rows brings
-// all four planes of a chunk and the MMA selects a plane by a 32-byte offset.
-// In the TF32 form the 128 B are re and im of the chunk as TF32 (64 B each);
-// the same offsets then select (re, K 0-7), (re, K 8-15), (im, K 0-7), (im,
-// K 8-15), and a chunk takes 8 MMAs (K = 8) instead of 12.
+// Operand rows: one row per (position x, component c), row NC x + c (NC = 4
+// components, or 2 for two-component systems), holding for each 16-orbital
+// chunk the four split planes re_hi, re_lo, im_hi, im_lo side by side
+// (128 B), so one 128-byte-swizzled TMA box of 128 rows brings all four
+// planes of a chunk and the MMA selects a plane by a 32-byte offset.  In the
+// TF32 form the 128 B are re and im of the chunk as TF32 (64 B each); the
+// same offsets then select (re, K 0-7), (re, K 8-15), (im, K 0-7), (im, K 8-15).
+// The i-multiplied rows iX = i X (planes -im, re: each row's two 64-byte
+// halves swapped, the new first half negated) are written beside them.
 //
-// Work item = (tile of 16 x 16 walker pairs, time).  Per item the tensor
-// cores accumulate G- (K = n_occ) and then G+ (K = n_vir) as 128 x 128
-// complex blocks (rows 8p + 4e + c of the p-pairs, columns 8q + 4e' + d of
-// the q-pairs) in one 256-column half of tensor memory.  Two epilogue
-// groups take alternate items, each with its own half: while one group
-// traces item i, the MMA warp fills the other half with item i+1.  G- is
+// The kernel runs on CTA pairs (clusters of two CTAs on the two SMs of a
+// TPC).  Work item = (pair tile, time); a pair tile is two p-blocks x one
+// q-block of TP walker pairs (TP = 16, or 32 for two-component systems, so
+// that a block is 128 operand rows): CTA r owns p-block bp = 2 BP + r, whose
+// 128 rows are its half of the A operand of an M = 256 MMA, and holds the
+// q-block's 128 rows as its half of the B operand, CTA 0 from X and CTA 1 from
+// iX.  One thread of the even CTA issues cta_group::2 MMAs with M = N = 256:
+// with A = X_re planes and B = [Y; iY]_re planes, then A = X_im and B =
+// [Y; iY]_im, one accumulator of 256 columns collects
+//   [Xr Yr^T + Xi Yi^T | Xi Yr^T - Xr Yi^T] = [Re G | Im G],
+// each real product as hi*hi + hi*lo + lo*hi (6 MMAs per 16-orbital chunk;
+// 4 TF32 MMAs).  Each CTA's tensor memory thus holds the 128 x 128 complex
+// blocks of its own TP x TP tile (rows NC(2p + e) + c, columns NC(2q + e') + d),
+// Re in the group's first 128 columns and Im in the next 128.
+//
+// Per item the tensor cores accumulate G- (K = n_occ) and then G+
+// (K = n_vir) in one 256-column half of tensor memory.  Two epilogue groups
+// per CTA take alternate items, each with its own half: while one group
+// traces item i, the MMAs fill the other half with item i+1.  G- is
 // accumulated first in the same columns; its group copies the like-electron
 // blocks G-(ep, eq) (the only G- blocks the trace form needs) to shared
-// memory at once, which frees the columns for G+.  With PR_GM_PACKED they
-// are kept there as 24-bit floats (FP32 rounded to 15 stored significand
-// bits, relative error at most 2^-16, about the error the split BF16
-// products already carry), which leaves room for a fourth operand stage.
-constexpr int PR_BK = 16;                          // orbitals per chunk (one stage)
-constexpr int PR_TILE_BYTES = 128 * 4 * PR_BK * 2; // 128 rows x (4 planes x 16 BF16) = 16 KB
-constexpr bool PR_GM_PACKED = true;                // G- kept as 24-bit floats
-constexpr int PR_STAGES = PR_GM_PACKED ? 4 : 3;
-constexpr int PR_STAGE_BYTES = 2 * PR_TILE_BYTES;  // A chunk, then B chunk
+// memory as 24-bit floats (FP32 rounded to 15 stored significand bits,
+// relative error at most 2^-16, about the error the split BF16 products
+// already carry), which frees the columns for G+.
+//
+// Barriers: each CTA's copies complete on its own stage barrier; a relay
+// thread of the odd CTA forwards that completion to the even CTA's stage
+// barrier, on which the MMA issuer waits (so each CTA can always drain its
+// own copies).  MMA completion is multicast to both CTAs (stage free, G-
+// ready, G+ ready); both CTAs' epilogue warps arrive on the even CTA's
+// barriers when they have unloaded G- or released the columns.
+constexpr int PR_BK = 16;                           // orbitals per chunk (one stage)
+constexpr int PR_TILE_BYTES = 128 * 4 * PR_BK * 2;  // 128 rows x (4 planes x 16 BF16) = 16 KB
+constexpr int PR_STAGES = 4;
+constexpr int PR_STAGE_BYTES = 2 * PR_TILE_BYTES;   // A chunk, then this CTA's B chunk
 constexpr int PR_GROUPS = 2;
-constexpr int PR_GROUP_WARPS = 8;                  // two per tensor-memory lane quarter
+constexpr int PR_GROUP_WARPS = 8;                   // two per tensor-memory lane quarter
 constexpr int PR_EPI_WARPS = PR_GROUPS * PR_GROUP_WARPS;
 constexpr int PR_THREADS = 64 + 32 * PR_EPI_WARPS;
-constexpr int PR_TMEM_COLS = 512;                  // per group: re | im of 128 columns
-// G- like blocks of one item: [16 q][3][128 rows] uint2 (8 x 24 bit) or [16 q][2][128 rows] float4
-constexpr int PR_GM_BYTES = PR_GM_PACKED ? 16 * 3 * 128 * 8 : 16 * 2 * 128 * 16;
+constexpr int PR_TMEM_COLS = 512;                   // per group: re | im of 128 columns
+constexpr int PR_GM_BYTES = 16 * 3 * 128 * 8;       // G- like blocks of one item: 48 KB
 constexpr int PR_GM_OFF = PR_STAGES * PR_STAGE_BYTES;
 constexpr int PR_BARS_OFF = PR_GM_OFF + PR_GROUPS * PR_GM_BYTES;
-constexpr int PR_RED_OFF = PR_BARS_OFF + 192;      // barriers + tensor-memory slot
+constexpr int PR_RED_OFF = PR_BARS_OFF + 192;       // barriers + tensor-memory slot
 constexpr int PR_SMEM = PR_RED_OFF + PR_GROUPS * 64 * 8 + 1024;
 static_assert(PR_SMEM <= 232448, "contraction kernel exceeds the shared memory of one CTA");
+static_assert(PR_STAGE_BYTES % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
 static_assert((2 * PR_STAGES + 4 * PR_GROUPS) * 8 + 4 <= 192, "barrier block too small");
 
 struct PairMaps {
-    CUtensorMap occ, vir;  // 3-D: (chunk x plane x orbital, row, tau), 64 x 128 boxes, 128-byte swizzle
+    // 3-D (chunk x plane x orbital, row, tau), 128-byte swizzle, 64 x 128-row boxes:
+    // X (occupied, virtual) and iX (occupied, virtual).
+    CUtensorMap occ, vir, iocc, ivir;
 };
 
 struct PairArgs {
     const double *a;   // [m] pair weight factors N_g / (g1 g2)
-    double *partials;  // [n_tau][n_tiles]
+    double *partials;  // [n_tau][n_tiles], one per TP x TP tile (bp <= bq)
     int *abort_flag;
-    int m, n_tiles, nb, n_tau, n_occ, n_vir;
+    int m, n_tiles, n_ptiles, nb, n_tau, n_occ, n_vir;
     double inv_lambda;
     unsigned long long timeout_ns;  // limit of every wait
     int withhold_first_copy;        // test hook: never issue the first stage's copy (its wait runs out)
 };
 
-__device__ __forceinline__ void pair_tile(int tile, int nb, int &bp, int &bq)
+// Pair tile k -> (BP, bq): row BP of the enumeration holds bq = 2 BP .. nb - 1.
+__device__ __forceinline__ void pair_tile(int k, int nb, int &BP, int &bq)
 {
-    int k = tile, b = 0;
-    while (k >= nb - b) {
-        k -= nb - b;
+    int b = 0;
+    while (k >= nb - 2 * b) {
+        k -= nb - 2 * b;
         ++b;
     }
-    bp = b;
-    bq = b + k;
+    BP = b;
+    bq = 2 * b + k;
 }
+
+// Index of the TP x TP tile (bp <= bq) in the row-by-row enumeration of the upper triangle.
+__device__ __forceinline__ int tile_index(int bp, int bq, int nb) { return bp * nb - bp * (bp - 1) / 2 + (bq - bp); }
 
 __device__ __forceinline__ int pr_chunks(int k) { return (k + PR_BK - 1) / PR_BK; }
 
@@ -485,14 +526,192 @@ __device__ __forceinline__ void group_sync(int g)
         bar_sync<2, 32 * PR_GROUP_WARPS>();
 }
 
+__device__ __forceinline__ uint32_t cluster_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_count()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+// Where an epilogue group stands: its CTA's rank in the pair, the cluster's item
+// sequence, and the even CTA's hand-off barriers (shared::cluster addresses).
+struct EpiCtx {
+    int rank, cid, ncl, n_items;
+    uint32_t munl_even, pfree_even;
+};
+
+// Trace epilogue of a four-component tile: rows 8p + 4e + c of 16 p-pairs,
+// columns 8q + 4e' + d of 16 q-pairs; the eight lanes (e, c) of a pair hold its rows.
+__device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned char *smem, uint32_t tmem,
+                                                  int warp, int lane, const EpiCtx &ec, uint64_t *mfull,
+                                                  uint64_t *pfull)
+{
+    const int ew = warp - 2;
+    const int g = ew / PR_GROUP_WARPS;
+    const int gw = ew - g * PR_GROUP_WARPS;
+    const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+    const int qhalf = gw >> 2;     // q-pairs 8*qhalf .. +7 of the tile
+    const int row = 32 * quarter + lane;
+    const int p_local = row >> 3, e = (row >> 2) & 1, c = lane & 3;
+    const int gbase = lane & ~7;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + 256u * g;
+    unsigned char *gm = smem + PR_GM_OFF + g * PR_GM_BYTES;
+    double *red = reinterpret_cast<double *>(smem + PR_RED_OFF) + 64 * g;
+    uint32_t ph = 0;
+    for (int item = ec.cid + g * ec.ncl; item < ec.n_items; item += PR_GROUPS * ec.ncl) {
+        const int t = item / args.n_ptiles, pt = item - t * args.n_ptiles;
+        int BP, bq;
+        pair_tile(pt, args.nb, BP, bq);
+        const int bp = 2 * BP + ec.rank;
+        // (1) G- like-electron blocks of this lane's row -> shared memory: for q, the
+        //     four entries G-(row, 8q + 4e + d) in the order re 0, im 0, re 1, im 1 |
+        //     re 2, im 2, re 3, im 3, packed to 24 bits as three uint2.
+        const bool got_m = mbar_wait(&mfull[g], ph, args.abort_flag, 4, args.timeout_ns);
+        if (group_any(g, !got_m)) break;  // the group leaves together
+        fence_after();
+#pragma unroll 1
+        for (int qb = 0; qb < 4; ++qb) {
+            const int q0 = 8 * qhalf + 2 * qb;
+            float vr[16], vi[16];
+            tmem_ld<16>(lane_addr + 8u * q0, vr);
+            tmem_ld<16>(lane_addr + 128u + 8u * q0, vi);
+            tmem_wait_ld();
+#pragma unroll
+            for (int qq = 0; qq < 2; ++qq) {
+                float o_r[4], o_i[4];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    o_r[d] = e ? vr[8 * qq + 4 + d] : vr[8 * qq + d];
+                    o_i[d] = e ? vi[8 * qq + 4 + d] : vi[8 * qq + d];
+                }
+                const int q = q0 + qq;
+                uint2 *gp = reinterpret_cast<uint2 *>(gm);
+                const uint3 u = pack24(o_r[0], o_i[0], o_r[1], o_i[1]);
+                const uint3 v = pack24(o_r[2], o_i[2], o_r[3], o_i[3]);
+                gp[(3 * q + 0) * 128 + row] = make_uint2(u.x, u.y);
+                gp[(3 * q + 1) * 128 + row] = make_uint2(u.z, v.x);
+                gp[(3 * q + 2) * 128 + row] = make_uint2(v.y, v.z);
+            }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(ec.munl_even);
+        // (2) traces once G+ is in the same columns.
+        const bool got_p = mbar_wait(&pfull[g], ph, args.abort_flag, 6, args.timeout_ns);
+        if (group_any(g, !got_p)) break;
+        ph ^= 1u;
+        fence_after();
+        const int p = bp * 16 + p_local;
+        // a_q of the tile's 16 q-pairs, one per lane (lane & 15), fetched by shuffle below.
+        const int q_lane = bq * 16 + (lane & 15);
+        const double a_lane = q_lane < args.m ? args.a[q_lane] : 0.0;
+        double acc = 0.0;  // sum over this warp's q of Re f_pq a_q
+#pragma unroll 1
+        for (int qb = 0; qb < 4; ++qb) {
+            const int q0 = 8 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
+            float gpr[16], gpi[16];
+            tmem_ld<16>(lane_addr + 8u * q0, gpr);
+            tmem_ld<16>(lane_addr + 128u + 8u * q0, gpi);
+            tmem_wait_ld();
+#pragma unroll
+            for (int qq = 0; qq < 2; ++qq) {
+                // This lane holds row c of G-(xe, ye) [own], G+(xe, ye) [dia], G+(xe, y(1-e)) [off].
+                const int ql = q0 + qq;
+                float own_r[4], own_i[4];
+                {
+                    const uint2 *gp = reinterpret_cast<const uint2 *>(gm);
+                    const uint2 w0 = gp[(3 * ql + 0) * 128 + row];
+                    const uint2 w1 = gp[(3 * ql + 1) * 128 + row];
+                    const uint2 w2 = gp[(3 * ql + 2) * 128 + row];
+                    unpack24(w0.x, w0.y, w1.x, own_r[0], own_i[0], own_r[1], own_i[1]);
+                    unpack24(w1.y, w2.x, w2.y, own_r[2], own_i[2], own_r[3], own_i[3]);
+                }
+                float dia_r[4], dia_i[4], off_r[4], off_i[4];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {  // constant indices keep the arrays in registers
+                    const int i0 = 8 * qq + d, i1 = 8 * qq + 4 + d;
+                    dia_r[d] = e ? gpr[i1] : gpr[i0];
+                    dia_i[d] = e ? gpi[i1] : gpi[i0];
+                    off_r[d] = e ? gpr[i0] : gpr[i1];
+                    off_i[d] = e ? gpi[i0] : gpi[i1];
+                }
+                // Direct: T_e = sum_cd conj(G-_cd) G+_cd over the like-electron block.
+                float tr = 0.f, ti = 0.f;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    tr += own_r[d] * dia_r[d] + own_i[d] * dia_i[d];
+                    ti += own_r[d] * dia_i[d] - own_i[d] * dia_r[d];
+                }
+                tr += __shfl_xor_sync(0xffffffffu, tr, 1);
+                ti += __shfl_xor_sync(0xffffffffu, ti, 1);
+                tr += __shfl_xor_sync(0xffffffffu, tr, 2);
+                ti += __shfl_xor_sync(0xffffffffu, ti, 2);
+                const float ur = __shfl_xor_sync(0xffffffffu, tr, 4);
+                const float ui = __shfl_xor_sync(0xffffffffu, ti, 4);
+                const float direct_re = tr * ur - ti * ui;
+                // Exchange: tr[G-(1q,1p) G+(1p,2q) G-(2q,2p) G+(2p,1q)] = sum_{c,c''} U_{cc''} V_{c''c},
+                // U = G+(1p,2q) G-(2p,2q)^dag, V = G+(2p,1q) G-(1p,1q)^dag.  Lane (e, c) pairs its
+                // rows with lane (1-e, c''): e = 0 takes c'' - c = 0, 1 and e = 1 takes 2, 3 (mod 4).
+                float xr = 0.f;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int src = gbase + (e == 0 ? 4 + ((c + s) & 3) : ((c + 2 - s) & 3));
+                    float rg_r[4], rg_i[4], ro_r[4], ro_i[4];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        rg_r[d] = __shfl_sync(0xffffffffu, own_r[d], src);
+                        rg_i[d] = __shfl_sync(0xffffffffu, own_i[d], src);
+                        ro_r[d] = __shfl_sync(0xffffffffu, off_r[d], src);
+                        ro_i[d] = __shfl_sync(0xffffffffu, off_i[d], src);
+                    }
+                    float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        a1r += off_r[d] * rg_r[d] + off_i[d] * rg_i[d];
+                        a1i += off_i[d] * rg_r[d] - off_r[d] * rg_i[d];
+                        a2r += ro_r[d] * own_r[d] + ro_i[d] * own_i[d];
+                        a2i += ro_i[d] * own_r[d] - ro_r[d] * own_i[d];
+                    }
+                    xr += a1r * a2r - a1i * a2i;
+                }
+                xr += __shfl_xor_sync(0xffffffffu, xr, 1);
+                xr += __shfl_xor_sync(0xffffffffu, xr, 2);
+                xr += __shfl_xor_sync(0xffffffffu, xr, 4);
+                const int q = bq * 16 + ql;
+                const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
+                const bool valid = p < args.m && q < args.m && (bp < bq || (bp == bq && p_local < ql));
+                if (valid) acc += (double)(-0.5f * (direct_re - xr)) * a_q;
+            }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(ec.pfree_even);
+        if ((lane & 7) == 0) red[16 * qhalf + 4 * quarter + (lane >> 3)] = (p < args.m) ? acc * args.a[p] : 0.0;
+        group_sync(g);
+        if (gw == 0 && lane == 0 && bp <= bq) {
+            double sum = 0.0;
+            for (int j = 0; j < 32; ++j) sum += red[j];
+            args.partials[(size_t)t * args.n_tiles + tile_index(bp, bq, args.nb)] = sum * args.inv_lambda;
+        }
+        group_sync(g);
+    }
+}
+
 // Trace epilogue of a two-component tile (NC = 2): rows 4p + 2e + c of 32
 // p-pairs, columns 4q + 2e' + d of 32 q-pairs, so the four lanes (e, c) of a
 // pair hold its rows.  Same hand-offs as the four-component epilogue: unload
 // the like-electron blocks G-(ep, eq) (2 x 2) to shared memory as 24-bit
 // floats, then trace against G+ once it is in the same columns.
 __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned char *smem, uint32_t tmem,
-                                                  int warp, int lane, int n_items, uint64_t *mfull,
-                                                  uint64_t *munl, uint64_t *pfull, uint64_t *pfree)
+                                                  int warp, int lane, const EpiCtx &ec, uint64_t *mfull,
+                                                  uint64_t *pfull)
 {
     const int ew = warp - 2;
     const int g = ew / PR_GROUP_WARPS;
@@ -506,10 +725,11 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
     uint32_t *gw32 = reinterpret_cast<uint32_t *>(smem + PR_GM_OFF + g * PR_GM_BYTES);  // [32 q][3][128 rows]
     double *red = reinterpret_cast<double *>(smem + PR_RED_OFF) + 64 * g;
     uint32_t ph = 0;
-    for (int item = blockIdx.x + g * gridDim.x; item < n_items; item += PR_GROUPS * gridDim.x) {
-        const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
-        int bp, bq;
-        pair_tile(tile, args.nb, bp, bq);
+    for (int item = ec.cid + g * ec.ncl; item < ec.n_items; item += PR_GROUPS * ec.ncl) {
+        const int t = item / args.n_ptiles, pt = item - t * args.n_ptiles;
+        int BP, bq;
+        pair_tile(pt, args.nb, BP, bq);
+        const int bp = 2 * BP + ec.rank;
         // (1) G-(xe, ye) row c: entries d = 0, 1 (re, im), packed into three words per q.
         const bool got_m = mbar_wait(&mfull[g], ph, args.abort_flag, 4, args.timeout_ns);
         if (group_any(g, !got_m)) break;
@@ -534,7 +754,7 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
         }
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&munl[g]);
+        if (lane == 0) mbar_arrive_cluster(ec.munl_even);
         // (2) traces once G+ is in the same columns.
         const bool got_p = mbar_wait(&pfull[g], ph, args.abort_flag, 6, args.timeout_ns);
         if (group_any(g, !got_p)) break;
@@ -600,19 +820,19 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
                 xr += __shfl_xor_sync(0xffffffffu, xr, 2);
                 const int q = bq * 32 + ql;
                 const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
-                const bool valid = p < args.m && q < args.m && (bp < bq || p_local < ql);
+                const bool valid = p < args.m && q < args.m && (bp < bq || (bp == bq && p_local < ql));
                 if (valid) acc += (double)(-0.5f * (direct_re - xr)) * a_q;
             }
         }
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&pfree[g]);
+        if (lane == 0) mbar_arrive_cluster(ec.pfree_even);
         if ((lane & 3) == 0) red[32 * qhalf + 8 * quarter + (lane >> 2)] = (p < args.m) ? acc * args.a[p] : 0.0;
         group_sync(g);
-        if (gw == 0 && lane == 0) {
+        if (gw == 0 && lane == 0 && bp <= bq) {
             double sum = 0.0;
             for (int j = 0; j < 64; ++j) sum += red[j];
-            args.partials[(size_t)t * args.n_tiles + tile] = sum * args.inv_lambda;
+            args.partials[(size_t)t * args.n_tiles + tile_index(bp, bq, args.nb)] = sum * args.inv_lambda;
         }
         group_sync(g);
     }
@@ -627,57 +847,70 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + PR_BARS_OFF);
     uint64_t *empty = full + PR_STAGES;
-    uint64_t *mfull = empty + PR_STAGES;  // [group] G- accumulated
-    uint64_t *munl = mfull + PR_GROUPS;   // [group] G- copied out (8 warps)
-    uint64_t *pfull = munl + PR_GROUPS;   // [group] G+ accumulated
-    uint64_t *pfree = pfull + PR_GROUPS;  // [group] columns free again (8 warps)
+    uint64_t *mfull = empty + PR_STAGES;  // [group] G- accumulated (both CTAs)
+    uint64_t *munl = mfull + PR_GROUPS;   // [group] G- copied out (even CTA: 8 warps x 2 CTAs)
+    uint64_t *pfull = munl + PR_GROUPS;   // [group] G+ accumulated (both CTAs)
+    uint64_t *pfree = pfull + PR_GROUPS;  // [group] columns free again (even CTA: 8 warps x 2 CTAs)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pfree + PR_GROUPS);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int cid = (int)cluster_id(), ncl = (int)cluster_count();
     const int n_occ_chunks = pr_chunks(args.n_occ), n_vir_chunks = pr_chunks(args.n_vir);
     const int n_occ_stages = n_occ_chunks;
     const int stages_per_tile = n_occ_chunks + n_vir_chunks;
-    const int n_items = args.n_tiles * args.n_tau;
+    const int n_items = args.n_ptiles * args.n_tau;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < PR_STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], leader ? 2 : 1);  // even CTA: its own copies + the odd CTA's relay
             mbar_init(&empty[s], 1);
         }
         for (int g = 0; g < PR_GROUPS; ++g) {
             mbar_init(&mfull[g], 1);
-            mbar_init(&munl[g], PR_GROUP_WARPS);
+            mbar_init(&munl[g], 2 * PR_GROUP_WARPS);
             mbar_init(&pfull[g], 1);
-            mbar_init(&pfree[g], PR_GROUP_WARPS);
+            mbar_init(&pfree[g], 2 * PR_GROUP_WARPS);
         }
         mbar_init_fence();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, PR_TMEM_COLS);
+    if (warp == 1) tmem_alloc_pair(tmem_slot, PR_TMEM_COLS);
     fence_before();
     __syncthreads();
+    cluster_sync();  // barriers of both CTAs initialised before any remote arrive or multicast commit
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ---------------- TMA producer ----------------
+        // ---------------- TMA producer (both CTAs) ----------------
         if (lane == 0) {
+            const CUtensorMap *b_occ = leader ? &maps.occ : &maps.iocc;  // B half: Y (even CTA) or iY (odd)
+            const CUtensorMap *b_vir = leader ? &maps.vir : &maps.ivir;
             tma_prefetch(&maps.occ);
             tma_prefetch(&maps.vir);
+            tma_prefetch(b_occ);
+            tma_prefetch(b_vir);
             int stage = 0;
             uint32_t phase = 0;
             int issued[PR_STAGES] = {};
             uint32_t issued_phase[PR_STAGES] = {};
             bool ok = true;
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
-                int bp, bq;
-                pair_tile(tile, args.nb, bp, bq);
+            for (int item = cid; item < n_items && ok; item += ncl) {
+                const int t = item / args.n_ptiles, pt = item - t * args.n_ptiles;
+                int BP, bq;
+                pair_tile(pt, args.nb, BP, bq);
+                // A CTA without a p-block (odd block count) loads the last block instead;
+                // its results are discarded.
+                const int bp = 2 * BP + (int)rank;
+                const int a_row = (bp < args.nb ? bp : args.nb - 1) * 128;
+                const int b_row = bq * 128;
                 for (int c = 0; c < stages_per_tile; ++c) {
                     if (!mbar_wait_fast(&empty[stage], phase ^ 1u, args.abort_flag, 1, args.timeout_ns)) {
                         ok = false;
                         break;
                     }
-                    if (args.withhold_first_copy && item == (int)blockIdx.x && c == 0) {
+                    if (args.withhold_first_copy && item == cid && c == 0) {
                         // Test hook: skip this stage entirely; nothing completes its barrier.
                         if (++stage == PR_STAGES) {
                             stage = 0;
@@ -687,11 +920,10 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                     }
                     const bool occ = c < n_occ_stages;
                     const int x = (occ ? c : c - n_occ_stages) * 4 * PR_BK;
-                    const CUtensorMap *mp = occ ? &maps.occ : &maps.vir;
                     unsigned char *st = smem + stage * PR_STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[stage], PR_STAGE_BYTES);
-                    tma_load_3d(st, mp, &full[stage], x, bp * 128, t);
-                    tma_load_3d(st + PR_TILE_BYTES, mp, &full[stage], x, bq * 128, t);
+                    tma_load_3d(st, occ ? &maps.occ : &maps.vir, &full[stage], x, a_row, t);
+                    tma_load_3d(st + PR_TILE_BYTES, occ ? b_occ : b_vir, &full[stage], x, b_row, t);
                     issued[stage] = 1;
                     issued_phase[stage] = phase;
                     if (++stage == PR_STAGES) {
@@ -704,15 +936,35 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                 for (int s = 0; s < PR_STAGES; ++s)
                     if (issued[s]) mbar_drain(&full[s], issued_phase[s], args.timeout_ns);
         }
+    } else if (warp == 1 && !leader) {
+        // ---------------- relay (odd CTA): its copies landed -> the even CTA's stage barrier ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int item = cid; item < n_items && ok; item += ncl) {
+                for (int c = 0; c < stages_per_tile; ++c) {
+                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 7, args.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_shared(&full[stage], 0));
+                    if (++stage == PR_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer (even CTA) ----------------
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
             uint32_t use[PR_GROUPS] = {0, 0};  // parity of each group's uses so far
             bool ok = true;
-            const uint32_t id_pos = TF32 ? idesc_tf32(128, false) : idesc_bf16(128, false);
-            const uint32_t id_neg = TF32 ? idesc_tf32(128, true) : idesc_bf16(128, true);
+            const uint32_t id = idesc_pair(TF32 ? idesc_tf32(256, false) : idesc_bf16(256, false));
+            constexpr uint16_t BOTH = 3;
             // Descriptors of stage 0; stage s adds s * PR_STAGE_BYTES to the start-address
             // field (address >> 4 in the low 14 bits, no carry for addresses below 256 KB).
             // Keeping this loop short matters: the tensor pipe drains while it runs.
@@ -723,9 +975,9 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             const uint64_t brh0 = sdesc_sw128(base0 + BOFF + 0), brl0 = sdesc_sw128(base0 + BOFF + 32);
             const uint64_t bih0 = sdesc_sw128(base0 + BOFF + 64), bil0 = sdesc_sw128(base0 + BOFF + 96);
             int li = 0;
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++li) {
+            for (int item = cid; item < n_items && ok; item += ncl, ++li) {
                 const int g = li & 1;
-                const uint32_t d_re = tmem + 256u * g, d_im = d_re + 128u;
+                const uint32_t d = tmem + 256u * g;  // [Re G | Im G]
                 if (!mbar_wait_fast(&pfree[g], use[g] ^ 1u, args.abort_flag, 2, args.timeout_ns)) {
                     ok = false;
                     break;
@@ -733,8 +985,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                 fence_after();
                 for (int c = 0; c < stages_per_tile; ++c) {
                     if (c == n_occ_stages) {
-                        // G- complete: hand it to the group, then reuse the columns for G+.
-                        umma_commit(&mfull[g]);
+                        // G- complete: hand it to both CTAs' groups, then reuse the columns for G+.
+                        umma_pair_commit(&mfull[g], BOTH);
                         if (!mbar_wait_fast(&munl[g], use[g], args.abort_flag, 5, args.timeout_ns)) {
                             ok = false;
                             break;
@@ -750,216 +1002,51 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                     const uint64_t arh = arh0 + so, arl = arl0 + so, aih = aih0 + so, ail = ail0 + so;
                     const uint64_t brh = brh0 + so, brl = brl0 + so, bih = bih0 + so, bil = bil0 + so;
                     const uint32_t acc = (c == 0 || c == n_occ_stages) ? 0u : 1u;
-                    // Re G += Xr Yr^T + Xi Yi^T and Im G += Xi Yr^T - Xr Yi^T, alternating
-                    // between the two accumulators.  (Straight-line code: the issue loop
-                    // must stay short, the tensor pipe drains while it runs.)
+                    // [Re | Im] += X_re [Y; iY]_re^T + X_im [Y; iY]_im^T (straight-line code:
+                    // the issue loop must stay short, the tensor pipe drains while it runs).
                     if constexpr (TF32) {
                         // descriptors at +0, +32, +64, +96: re K 0-7, re K 8-15, im K 0-7, im K 8-15
-                        umma_tf32(d_re, arh, brh, id_pos, acc);
-                        umma_tf32(d_im, aih, brh, id_pos, acc);
-                        umma_tf32(d_re, aih, bih, id_pos, 1u);
-                        umma_tf32(d_im, arh, bih, id_neg, 1u);
-                        umma_tf32(d_re, arl, brl, id_pos, 1u);
-                        umma_tf32(d_im, ail, brl, id_pos, 1u);
-                        umma_tf32(d_re, ail, bil, id_pos, 1u);
-                        umma_tf32(d_im, arl, bil, id_neg, 1u);
+                        umma_pair_tf32(d, arh, brh, id, acc);
+                        umma_pair_tf32(d, arl, brl, id, 1u);
+                        umma_pair_tf32(d, aih, bih, id, 1u);
+                        umma_pair_tf32(d, ail, bil, id, 1u);
                     } else {
-                        umma(d_re, arh, brh, id_pos, acc);
-                        umma(d_im, aih, brh, id_pos, acc);
-                        umma(d_re, arh, brl, id_pos, 1u);
-                        umma(d_im, aih, brl, id_pos, 1u);
-                        umma(d_re, arl, brh, id_pos, 1u);
-                        umma(d_im, ail, brh, id_pos, 1u);
-                        umma(d_re, aih, bih, id_pos, 1u);
-                        umma(d_im, arh, bih, id_neg, 1u);
-                        umma(d_re, aih, bil, id_pos, 1u);
-                        umma(d_im, arh, bil, id_neg, 1u);
-                        umma(d_re, ail, bih, id_pos, 1u);
-                        umma(d_im, arl, bih, id_neg, 1u);
+                        umma_pair(d, arh, brh, id, acc);
+                        umma_pair(d, arh, brl, id, 1u);
+                        umma_pair(d, arl, brh, id, 1u);
+                        umma_pair(d, aih, bih, id, 1u);
+                        umma_pair(d, aih, bil, id, 1u);
+                        umma_pair(d, ail, bih, id, 1u);
                     }
-                    umma_commit(&empty[stage]);
+                    umma_pair_commit(&empty[stage], BOTH);
                     if (++stage == PR_STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
                 }
                 if (!ok) break;
-                umma_commit(&pfull[g]);
+                umma_pair_commit(&pfull[g], BOTH);
                 use[g] ^= 1u;
             }
-            umma_commit(&empty[stage]);
+            // Let every MMA this thread issued finish before tensor memory is freed.
+            umma_pair_commit(&empty[stage], 1);
             mbar_drain(&empty[stage], phase, args.timeout_ns);
         }
-    } else if constexpr (NC == 2) {
-        pairs_epilogue_2c(args, smem, tmem, warp, lane, n_items, mfull, munl, pfull, pfree);
     } else {
-        // ---------------- epilogue: two groups of 8 warps, alternate items ----------------
-        const int ew = warp - 2;
-        const int g = ew / PR_GROUP_WARPS;
-        const int gw = ew - g * PR_GROUP_WARPS;
-        const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
-        const int qhalf = gw >> 2;     // q-pairs 8*qhalf .. +7 of the tile
-        const int row = 32 * quarter + lane;
-        const int p_local = row >> 3, e = (row >> 2) & 1, c = lane & 3;
-        const int gbase = lane & ~7;
-        const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + 256u * g;
-        unsigned char *gm = smem + PR_GM_OFF + g * PR_GM_BYTES;
-        double *red = reinterpret_cast<double *>(smem + PR_RED_OFF) + 32 * g;
-        uint32_t ph = 0;
-        for (int item = blockIdx.x + g * gridDim.x; item < n_items; item += PR_GROUPS * gridDim.x) {
-            const int t = item / args.n_tiles, tile = item - t * args.n_tiles;
-            int bp, bq;
-            pair_tile(tile, args.nb, bp, bq);
-            // (1) G- like-electron blocks of this lane's row -> shared memory: for q, the
-            //     four entries G-(row, 8q + 4e + d) in the order re 0, im 0, re 1, im 1 |
-            //     re 2, im 2, re 3, im 3, as two float4 or, packed to 24 bits, three uint2.
-            const bool got_m = mbar_wait(&mfull[g], ph, args.abort_flag, 4, args.timeout_ns);
-            if (group_any(g, !got_m)) break;  // the group leaves together
-            fence_after();
-#pragma unroll 1
-            for (int qb = 0; qb < 4; ++qb) {
-                const int q0 = 8 * qhalf + 2 * qb;
-                float vr[16], vi[16];
-                tmem_ld<16>(lane_addr + 8u * q0, vr);
-                tmem_ld<16>(lane_addr + 128u + 8u * q0, vi);
-                tmem_wait_ld();
-#pragma unroll
-                for (int qq = 0; qq < 2; ++qq) {
-                    float o_r[4], o_i[4];
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        o_r[d] = e ? vr[8 * qq + 4 + d] : vr[8 * qq + d];
-                        o_i[d] = e ? vi[8 * qq + 4 + d] : vi[8 * qq + d];
-                    }
-                    const int q = q0 + qq;
-                    if constexpr (PR_GM_PACKED) {
-                        uint2 *gp = reinterpret_cast<uint2 *>(gm);
-                        const uint3 u = pack24(o_r[0], o_i[0], o_r[1], o_i[1]);
-                        const uint3 v = pack24(o_r[2], o_i[2], o_r[3], o_i[3]);
-                        gp[(3 * q + 0) * 128 + row] = make_uint2(u.x, u.y);
-                        gp[(3 * q + 1) * 128 + row] = make_uint2(u.z, v.x);
-                        gp[(3 * q + 2) * 128 + row] = make_uint2(v.y, v.z);
-                    } else {
-                        float4 *gf = reinterpret_cast<float4 *>(gm);
-                        gf[(2 * q + 0) * 128 + row] = make_float4(o_r[0], o_i[0], o_r[1], o_i[1]);
-                        gf[(2 * q + 1) * 128 + row] = make_float4(o_r[2], o_i[2], o_r[3], o_i[3]);
-                    }
-                }
-            }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&munl[g]);
-            // (2) traces once G+ is in the same columns.
-            const bool got_p = mbar_wait(&pfull[g], ph, args.abort_flag, 6, args.timeout_ns);
-            if (group_any(g, !got_p)) break;
-            ph ^= 1u;
-            fence_after();
-            const int p = bp * 16 + p_local;
-            // a_q of the tile's 16 q-pairs, one per lane (lane & 15), fetched by shuffle below.
-            const int q_lane = bq * 16 + (lane & 15);
-            const double a_lane = q_lane < args.m ? args.a[q_lane] : 0.0;
-            double acc = 0.0;  // sum over this warp's q of Re f_pq a_q
-#pragma unroll 1
-            for (int qb = 0; qb < 4; ++qb) {
-                const int q0 = 8 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
-                float gpr[16], gpi[16];
-                tmem_ld<16>(lane_addr + 8u * q0, gpr);
-                tmem_ld<16>(lane_addr + 128u + 8u * q0, gpi);
-                tmem_wait_ld();
-#pragma unroll
-                for (int qq = 0; qq < 2; ++qq) {
-                    // This lane holds row c of G-(xe, ye) [own], G+(xe, ye) [dia], G+(xe, y(1-e)) [off].
-                    const int ql = q0 + qq;
-                    float own_r[4], own_i[4];
-                    if constexpr (PR_GM_PACKED) {
-                        const uint2 *gp = reinterpret_cast<const uint2 *>(gm);
-                        const uint2 w0 = gp[(3 * ql + 0) * 128 + row];
-                        const uint2 w1 = gp[(3 * ql + 1) * 128 + row];
-                        const uint2 w2 = gp[(3 * ql + 2) * 128 + row];
-                        unpack24(w0.x, w0.y, w1.x, own_r[0], own_i[0], own_r[1], own_i[1]);
-                        unpack24(w1.y, w2.x, w2.y, own_r[2], own_i[2], own_r[3], own_i[3]);
-                    } else {
-                        const float4 *gf = reinterpret_cast<const float4 *>(gm);
-                        const float4 m0 = gf[(2 * ql + 0) * 128 + row];
-                        const float4 m1 = gf[(2 * ql + 1) * 128 + row];
-                        own_r[0] = m0.x; own_i[0] = m0.y; own_r[1] = m0.z; own_i[1] = m0.w;
-                        own_r[2] = m1.x; own_i[2] = m1.y; own_r[3] = m1.z; own_i[3] = m1.w;
-                    }
-                    float dia_r[4], dia_i[4], off_r[4], off_i[4];
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {  // constant indices keep the arrays in registers
-                        const int i0 = 8 * qq + d, i1 = 8 * qq + 4 + d;
-                        dia_r[d] = e ? gpr[i1] : gpr[i0];
-                        dia_i[d] = e ? gpi[i1] : gpi[i0];
-                        off_r[d] = e ? gpr[i0] : gpr[i1];
-                        off_i[d] = e ? gpi[i0] : gpi[i1];
-                    }
-                    // Direct: T_e = sum_cd conj(G-_cd) G+_cd over the like-electron block.
-                    float tr = 0.f, ti = 0.f;
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        tr += own_r[d] * dia_r[d] + own_i[d] * dia_i[d];
-                        ti += own_r[d] * dia_i[d] - own_i[d] * dia_r[d];
-                    }
-                    tr += __shfl_xor_sync(0xffffffffu, tr, 1);
-                    ti += __shfl_xor_sync(0xffffffffu, ti, 1);
-                    tr += __shfl_xor_sync(0xffffffffu, tr, 2);
-                    ti += __shfl_xor_sync(0xffffffffu, ti, 2);
-                    const float ur = __shfl_xor_sync(0xffffffffu, tr, 4);
-                    const float ui = __shfl_xor_sync(0xffffffffu, ti, 4);
-                    const float direct_re = tr * ur - ti * ui;
-                    // Exchange: tr[G-(1q,1p) G+(1p,2q) G-(2q,2p) G+(2p,1q)] = sum_{c,c''} U_{cc''} V_{c''c},
-                    // U = G+(1p,2q) G-(2p,2q)^dag, V = G+(2p,1q) G-(1p,1q)^dag.  Lane (e, c) pairs its
-                    // rows with lane (1-e, c''): e = 0 takes c'' - c = 0, 1 and e = 1 takes 2, 3 (mod 4).
-                    float xr = 0.f;
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const int src = gbase + (e == 0 ? 4 + ((c + s) & 3) : ((c + 2 - s) & 3));
-                        float rg_r[4], rg_i[4], ro_r[4], ro_i[4];
-#pragma unroll
-                        for (int d = 0; d < 4; ++d) {
-                            rg_r[d] = __shfl_sync(0xffffffffu, own_r[d], src);
-                            rg_i[d] = __shfl_sync(0xffffffffu, own_i[d], src);
-                            ro_r[d] = __shfl_sync(0xffffffffu, off_r[d], src);
-                            ro_i[d] = __shfl_sync(0xffffffffu, off_i[d], src);
-                        }
-                        float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
-#pragma unroll
-                        for (int d = 0; d < 4; ++d) {
-                            a1r += off_r[d] * rg_r[d] + off_i[d] * rg_i[d];
-                            a1i += off_i[d] * rg_r[d] - off_r[d] * rg_i[d];
-                            a2r += ro_r[d] * own_r[d] + ro_i[d] * own_i[d];
-                            a2i += ro_i[d] * own_r[d] - ro_r[d] * own_i[d];
-                        }
-                        xr += a1r * a2r - a1i * a2i;
-                    }
-                    xr += __shfl_xor_sync(0xffffffffu, xr, 1);
-                    xr += __shfl_xor_sync(0xffffffffu, xr, 2);
-                    xr += __shfl_xor_sync(0xffffffffu, xr, 4);
-                    const int q = bq * 16 + ql;
-                    const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
-                    const bool valid = p < args.m && q < args.m && (bp < bq || p_local < ql);
-                    if (valid) acc += (double)(-0.5f * (direct_re - xr)) * a_q;
-                }
-            }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&pfree[g]);
-            if ((lane & 7) == 0) red[16 * qhalf + 4 * quarter + (lane >> 3)] = (p < args.m) ? acc * args.a[p] : 0.0;
-            group_sync(g);
-            if (gw == 0 && lane == 0) {
-                double sum = 0.0;
-                for (int j = 0; j < 32; ++j) sum += red[j];
-                args.partials[(size_t)t * args.n_tiles + tile] = sum * args.inv_lambda;
-            }
-            group_sync(g);
-        }
+        // ---------------- epilogue: two groups of 8 warps per CTA, alternate items ----------------
+        const int g = (warp - 2) / PR_GROUP_WARPS;
+        const EpiCtx ec{(int)rank, cid, ncl, n_items, mapa_shared(&munl[g], 0), mapa_shared(&pfree[g], 0)};
+        if constexpr (NC == 2)
+            pairs_epilogue_2c(args, smem, tmem, warp, lane, ec, mfull, pfull);
+        else
+            pairs_epilogue_4c(args, smem, tmem, warp, lane, ec, mfull, pfull);
     }
     fence_before();
     __syncthreads();
+    cluster_sync();  // no MMA, copy or remote arrive of either CTA is outstanding past this point
     if (warp == 1) {
         fence_after();
-        tmem_dealloc(tmem, PR_TMEM_COLS);
+        tmem_dealloc_pair(tmem, PR_TMEM_COLS);
     }
 }
 
@@ -1056,6 +1143,8 @@ MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t
     L.WTS_lo = take((size_t)L.wt_rows * L.nl3_pad * 2);
     L.occ_planes = take((size_t)n_tau * 4 * L.rows * L.k_occ_pad * 2);
     L.vir_planes = take((size_t)n_tau * 4 * L.rows * L.k_vir_pad * 2);
+    L.occ_iplanes = take((size_t)n_tau * 4 * L.rows * L.k_occ_pad * 2);
+    L.vir_iplanes = take((size_t)n_tau * 4 * L.rows * L.k_vir_pad * 2);
     L.flag = take(sizeof(int));
     L.end = off;
     return L;
@@ -1132,8 +1221,11 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
         const cuuint64_t sO[2] = {(cuuint64_t)L.k_occ_pad * 8, (cuuint64_t)L.rows * L.k_occ_pad * 8};
         const cuuint64_t dV[3] = {(cuuint64_t)4 * L.k_vir_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
         const cuuint64_t sV[2] = {(cuuint64_t)L.k_vir_pad * 8, (cuuint64_t)L.rows * L.k_vir_pad * 8};
-        if ((rc = encode(plan.maps_pairs[0], ws + L.occ_planes, 3, dO, sO, err, 4 * PR_BK, CU_TENSOR_MAP_SWIZZLE_128B)) ||
-            (rc = encode(plan.maps_pairs[1], ws + L.vir_planes, 3, dV, sV, err, 4 * PR_BK, CU_TENSOR_MAP_SWIZZLE_128B)))
+        const auto sw = CU_TENSOR_MAP_SWIZZLE_128B;
+        if ((rc = encode(plan.maps_pairs[0], ws + L.occ_planes, 3, dO, sO, err, 4 * PR_BK, sw)) ||
+            (rc = encode(plan.maps_pairs[1], ws + L.vir_planes, 3, dV, sV, err, 4 * PR_BK, sw)) ||
+            (rc = encode(plan.maps_pairs[2], ws + L.occ_iplanes, 3, dO, sO, err, 4 * PR_BK, sw)) ||
+            (rc = encode(plan.maps_pairs[3], ws + L.vir_iplanes, 3, dV, sV, err, 4 * PR_BK, sw)))
             return rc;
     }
     if (cudaFuncSetAttribute(spinor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM) !=
@@ -1148,6 +1240,29 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
             cudaSuccess) {
         err = "cannot reserve shared memory for the tensor-core kernels";
         return MCMP2_ECUDA;
+    }
+    // CTA pairs that fit on the device at once (one per TPC): the contraction's persistent grid.
+    {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cfg.gridDim = dim3(2 * (sms / 2));
+        cfg.blockDim = dim3(PR_THREADS);
+        cfg.dynamicSmemBytes = PR_SMEM;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, pairs_mixed_kernel<false, 4>, &cfg) != cudaSuccess || n < 1) {
+            err = "the contraction kernel's CTA pairs cannot be resident on this device";
+            return MCMP2_EUNSUPPORTED;
+        }
+        plan.pair_clusters = n;
     }
     plan.ready = true;
     return MCMP2_OK;
@@ -1174,7 +1289,7 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     SpinorMaps smaps;
     std::memcpy(&smaps, plan.maps_spinor, sizeof(smaps));
     const int n_mt = (L.P + 127) / 128;
-    SpinorArgs sa{scale, bf(L.occ_planes), bf(L.vir_planes), flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ,
+    SpinorArgs sa{scale, bf(L.occ_planes), bf(L.vir_planes), bf(L.occ_iplanes), bf(L.vir_iplanes), flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ,
                   s.n_occ, s.n_vir, s.n_orb, s.n_tau, L.rows, L.k_occ_pad, L.k_vir_pad, plan.tf32 ? 1 : 0,
                   plan.ncomp};
     const int sp_tiles = n_mt * plan.ncomp * L.n_kb;
@@ -1183,29 +1298,43 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     PairMaps pmaps;
     std::memcpy(&pmaps.occ, plan.maps_pairs[0], sizeof(CUtensorMap));
     std::memcpy(&pmaps.vir, plan.maps_pairs[1], sizeof(CUtensorMap));
+    std::memcpy(&pmaps.iocc, plan.maps_pairs[2], sizeof(CUtensorMap));
+    std::memcpy(&pmaps.ivir, plan.maps_pairs[3], sizeof(CUtensorMap));
     const int nb = pair_blocks(s.m, plan.ncomp == 2 ? TILE_PAIRS_MIXED_2C : TILE_PAIRS_MIXED);
     const int n_tiles = nb * (nb + 1) / 2;
-    PairArgs pa{a, partials, flag, s.m, n_tiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda, TIMEOUT_NS, 0};
+    int n_ptiles = 0;  // pair tiles: two p-blocks x one q-block, q-block >= the first p-block
+    for (int b = 0; 2 * b < nb; ++b) n_ptiles += nb - 2 * b;
+    PairArgs pa{a, partials, flag, s.m, n_tiles, n_ptiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda,
+                TIMEOUT_NS, 0};
     if (plan.withhold_once_ns) {
         pa.withhold_first_copy = 1;
         pa.timeout_ns = plan.withhold_once_ns;
         plan.withhold_once_ns = 0;
     }
-    const int items = n_tiles * s.n_tau;
+    const int items = n_ptiles * s.n_tau;
+    const int clusters = items < plan.pair_clusters ? items : plan.pair_clusters;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(PR_THREADS);
+    cfg.dynamicSmemBytes = PR_SMEM;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (ev) record_event(ev[0], st);
-    const int grid = items < sms ? items : sms;
-    if (plan.ncomp == 2) {
-        if (plan.tf32)
-            pairs_mixed_kernel<true, 2><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
-        else
-            pairs_mixed_kernel<false, 2><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
-    } else if (plan.tf32) {
-        pairs_mixed_kernel<true, 4><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
-    } else {
-        pairs_mixed_kernel<false, 4><<<grid, PR_THREADS, PR_SMEM, st>>>(pmaps, pa);
-    }
+    cudaError_t e;
+    if (plan.ncomp == 2)
+        e = plan.tf32 ? cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<true, 2>, pmaps, pa)
+                      : cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<false, 2>, pmaps, pa);
+    else
+        e = plan.tf32 ? cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<true, 4>, pmaps, pa)
+                      : cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<false, 4>, pmaps, pa);
     if (ev) record_event(ev[1], st);
-    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("mixed-form launch: ") + cudaGetErrorString(e);
         return MCMP2_ECUDA;
