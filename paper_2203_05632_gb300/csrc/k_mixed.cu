@@ -352,11 +352,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                 const int half = lane >> 4, piece = lane & 15;
                 const int ipiece = (piece & 8) | ((piece & 7) ^ 4);
                 const uint32_t flip = (piece & 4) ? 0u : neg;
+                // Chunks past the region's last orbital are never read by the contraction.
+                const bool real_chunk = k_first + 16 * (2 * jh + (piece >> 3)) < k_end;
 #pragma unroll 4
                 for (int it = 0; it < 16; ++it) {
                     const int row = 2 * it + half;
                     const int x = mt * 128 + 32 * quarter + row;
-                    if (x < args.P) {
+                    if (x < args.P && real_chunk) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * piece);
                         uint4 w = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * ipiece);
                         w.x ^= flip;
