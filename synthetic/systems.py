@@ -260,6 +260,12 @@ def _loewdin(C: np.ndarray, metric: np.ndarray) -> np.ndarray:
 # so the Monte Carlo estimate converges in seconds (used to pin the estimator).
 _SOFT_ZN = [(0, 0.05, 2.5, 5), (1, 0.05, 2.5, 4)]                  # 5 + 12 = 17
 _SOFT_H = [(0, 0.08, 2.5, 3)]                                        # 3
+# Soft variant of the medium system: the same shell counts (n_L = 300) with
+# the even-tempered ratio 1.4 instead of 2.5 (largest exponent 3.9 instead of
+# 7,450), so that with the soft energy windows no orbital is much tighter than
+# the weight function and the estimator has a finite variance.
+_SOFT_SN = [(0, 0.05, 1.4, 14), (1, 0.08, 1.4, 8), (2, 0.2, 1.4, 3)]
+_SOFT_CL = [(0, 0.05, 1.4, 8), (1, 0.08, 1.4, 6), (2, 0.2, 1.4, 2)]
 
 
 def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = False,
@@ -285,8 +291,8 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     for ic, z in enumerate(charges):
         recipe = _recipe(config, z)
         if soft:
-            assert config == "tiny", "the soft variant exists for the tiny system only"
-            recipe = {30: _SOFT_ZN, 1: _SOFT_H}[z]
+            assert config in ("tiny", "medium"), "soft variants exist for the tiny and medium systems"
+            recipe = {30: _SOFT_ZN, 1: _SOFT_H, 50: _SOFT_SN, 17: _SOFT_CL}[z]
         shells += _shells_for(ic, recipe)
     shell_centre = np.array([s[0] for s in shells], dtype=np.int32)
     shell_l = np.array([s[1] for s in shells], dtype=np.int32)

@@ -1,0 +1,30 @@
+"""The seeded input generators: sizes, energy windows and exponent ranges of the
+systems the tests and the benchmark draw (CPU only)."""
+import numpy as np
+
+import synthetic
+
+
+def test_medium_and_soft_medium_share_the_workload_sizes():
+    med = synthetic.make_system("medium")
+    soft = synthetic.make_system("medium", soft=True)
+    for s in (med, soft):
+        assert s.n_l == 300 and s.n_occ == 80 and s.n_vir == 400 and len(s.centres) == 6
+    # Soft: largest exponent within the weight function's reach, valence-like energies.
+    assert med.shell_alpha.max() > 1000.0
+    assert soft.shell_alpha.max() < 4.0
+    assert soft.eps[:80].min() >= -2.0 and soft.eps[:80].max() <= -0.3
+    assert soft.eps[80:].min() >= 0.1 and soft.eps[80:].max() <= 3.0
+    # Orthonormal 4-component spinors in the 4-component metric.
+    s_ll, s_ss = synthetic.overlap_matrices(soft)
+    n = soft.n_l
+    blocks = [soft.C[k * n:(k + 1) * n] for k in range(4)]
+    M = sum(b.conj().T @ S @ b for b, S in zip(blocks, (s_ll, s_ll, s_ss, s_ss)))
+    np.testing.assert_allclose(M, np.eye(soft.n_orb), atol=1e-9)
+
+
+def test_generators_are_seeded():
+    a = synthetic.make_system("medium", soft=True)
+    b = synthetic.make_system("medium", soft=True)
+    assert a.digest() == b.digest()
+    assert synthetic.make_system("medium", soft=True, seed=7).digest() != a.digest()
