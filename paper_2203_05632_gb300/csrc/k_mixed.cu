@@ -7,15 +7,17 @@
 //     real split-BF16 x3 GEMM, phi = [g | grad g] x W (W = C folded with the
 //     Pauli matrices), FP32 accumulate in tensor memory.  Its epilogue scales
 //     the spinor values by s_k(tau) for every imaginary time and writes the
-//     BF16 hi/lo planes of X(x)_ck = phi_k^c(x) s_k(tau): rows 4x + c,
-//     occupied and virtual orbitals in separate planes.
-//  3. pairs_mixed_kernel: for every (16 x 16 walker-pair tile, tau) the
+//     BF16 hi/lo planes (or TF32 values) of X(x)_ck = phi_k^c(x) s_k(tau),
+//     rows 4x + c (2x + c for two-component systems), occupied and virtual
+//     orbitals in separate planes, and the same rows of iX = i X.
+//  3. pairs_mixed_kernel, on CTA pairs: for every (pair tile, tau) the
 //     Hermitian products G(x, y)_cd = sum_k X(x)_ck conj(X(y)_dk) over the
-//     occupied (G-) and virtual (G+) orbitals,
-//       Re G = Xr Yr^T + Xi Yi^T,  Im G = Xi Yr^T - Xr Yi^T,
-//     each real product as hi*hi + hi*lo + lo*hi (12 MMAs per 16-deep K step),
-//     then the direct and exchange traces of the trace form of Eq. MCMP2 for
-//     every pair of pairs, accumulated in FP64 as Re f / (w w w).
+//     occupied (G-) and virtual (G+) orbitals as M = N = 256 MMAs whose B
+//     operand [Y; iY] yields [Re G | Im G] = [Xr Yr^T + Xi Yi^T | Xi Yr^T - Xr Yi^T]
+//     in one accumulator, each real product as hi*hi + hi*lo + lo*hi (6 MMAs
+//     per 16-deep K step; 4 in TF32), then the direct and exchange traces of
+//     the trace form of Eq. MCMP2 for every pair of pairs, accumulated in FP64
+//     as Re f / (w w w).
 // Every wait is bounded in time; on a time-out a kernel records it in a flag,
 // stops, drains its own copies, frees tensor memory and returns, and the host
 // reports MCMP2_ETIMEOUT.
