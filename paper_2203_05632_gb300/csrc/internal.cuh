@@ -8,8 +8,8 @@ namespace mcmp2 {
 
 // Pairs of walker pairs are processed in square tiles of TILE_PAIRS pairs per side.
 constexpr int TILE_PAIRS_F64 = 8;     // FP64 form: 64 x 64 complex position-component blocks
-constexpr int TILE_PAIRS_MIXED = 16;  // mixed form: 128 x 128 (one tcgen05 M = N = 128 tile)
-constexpr int TILE_PAIRS_MIXED_2C = 32;  // mixed form, two-component systems: 4 rows per pair in the same tile
+constexpr int TILE_PAIRS_MIXED = 16;  // mixed form: 128 operand rows per side (each CTA of a pair, M = N = 256 MMAs)
+constexpr int TILE_PAIRS_MIXED_2C = 32;  // mixed form, two-component systems: 4 rows per pair in the same 128 rows
 
 // Running statistics of the production steps (Eq. uncertainty), kept on the device.
 struct Stats {
