@@ -842,6 +842,34 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
     }
 }
 
+// Order in which a CTA pair contracts its chunks (producer and MMA issuer alike):
+// each item's G+ chunks, with the next item's G- chunks issued PR_TAIL chunks
+// before their end, so that the next group unloads its G- while these last G+
+// MMAs run instead of leaving the tensor pipe idle.  f(li, item, occ, c) is
+// called per chunk (li: the cluster's item counter) and returns false to stop.
+constexpr int PR_TAIL = 5;
+template <class F>
+__device__ __forceinline__ bool for_each_chunk(int cid, int ncl, int n_items, int n_occ_chunks, int n_vir_chunks,
+                                               F &&f)
+{
+    int li = 0;
+    for (int item = cid; item < n_items; item += ncl, ++li) {
+        const bool has_next = item + ncl < n_items;
+        if (li == 0)
+            for (int c = 0; c < n_occ_chunks; ++c)
+                if (!f(li, item, true, c)) return false;
+        const int tail = has_next ? (n_vir_chunks < PR_TAIL ? n_vir_chunks : PR_TAIL) : 0;
+        for (int c = 0; c < n_vir_chunks - tail; ++c)
+            if (!f(li, item, false, c)) return false;
+        if (has_next)
+            for (int c = 0; c < n_occ_chunks; ++c)
+                if (!f(li + 1, item + ncl, true, c)) return false;
+        for (int c = n_vir_chunks - tail; c < n_vir_chunks; ++c)
+            if (!f(li, item, false, c)) return false;
+    }
+    return true;
+}
+
 template <bool TF32, int NC>
 __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid_constant__ PairMaps maps,
                                                                     const PairArgs args)
@@ -862,7 +890,6 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
     const bool leader = rank == 0;
     const int cid = (int)cluster_id(), ncl = (int)cluster_count();
     const int n_occ_chunks = pr_chunks(args.n_occ), n_vir_chunks = pr_chunks(args.n_vir);
-    const int n_occ_stages = n_occ_chunks;
     const int stages_per_tile = n_occ_chunks + n_vir_chunks;
     const int n_items = args.n_ptiles * args.n_tau;
 
@@ -899,43 +926,42 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             uint32_t phase = 0;
             int issued[PR_STAGES] = {};
             uint32_t issued_phase[PR_STAGES] = {};
-            bool ok = true;
-            for (int item = cid; item < n_items && ok; item += ncl) {
-                const int t = item / args.n_ptiles, pt = item - t * args.n_ptiles;
-                int BP, bq;
-                pair_tile(pt, args.nb, BP, bq);
-                // A CTA without a p-block (odd block count) loads the last block instead;
-                // its results are discarded.
-                const int bp = 2 * BP + (int)rank;
-                const int a_row = (bp < args.nb ? bp : args.nb - 1) * 128;
-                const int b_row = bq * 128;
-                for (int c = 0; c < stages_per_tile; ++c) {
-                    if (!mbar_wait_fast(&empty[stage], phase ^ 1u, args.abort_flag, 1, args.timeout_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    if (args.withhold_first_copy && item == cid && c == 0) {
-                        // Test hook: skip this stage entirely; nothing completes its barrier.
-                        if (++stage == PR_STAGES) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
-                        continue;
-                    }
-                    const bool occ = c < n_occ_stages;
-                    const int x = (occ ? c : c - n_occ_stages) * 4 * PR_BK;
-                    unsigned char *st = smem + stage * PR_STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full[stage], PR_STAGE_BYTES);
-                    tma_load_3d(st, occ ? &maps.occ : &maps.vir, &full[stage], x, a_row, t);
-                    tma_load_3d(st + PR_TILE_BYTES, occ ? b_occ : b_vir, &full[stage], x, b_row, t);
-                    issued[stage] = 1;
-                    issued_phase[stage] = phase;
+            int cur_item = -1, t = 0, a_row = 0, b_row = 0;
+            const bool ok = for_each_chunk(cid, ncl, n_items, n_occ_chunks, n_vir_chunks,
+                                           [&](int li, int item, bool occ, int c) {
+                if (!mbar_wait_fast(&empty[stage], phase ^ 1u, args.abort_flag, 1, args.timeout_ns)) return false;
+                if (args.withhold_first_copy && li == 0 && occ && c == 0) {
+                    // Test hook: skip this stage entirely; nothing completes its barrier.
                     if (++stage == PR_STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
+                    return true;
                 }
-            }
+                if (item != cur_item) {
+                    cur_item = item;
+                    t = item / args.n_ptiles;
+                    int BP, bq;
+                    pair_tile(item - t * args.n_ptiles, args.nb, BP, bq);
+                    // A CTA without a p-block (odd block count) loads the last block instead;
+                    // its results are discarded.
+                    const int bp = 2 * BP + (int)rank;
+                    a_row = (bp < args.nb ? bp : args.nb - 1) * 128;
+                    b_row = bq * 128;
+                }
+                const int x = c * 4 * PR_BK;
+                unsigned char *st = smem + stage * PR_STAGE_BYTES;
+                mbar_arrive_expect_tx(&full[stage], PR_STAGE_BYTES);
+                tma_load_3d(st, occ ? &maps.occ : &maps.vir, &full[stage], x, a_row, t);
+                tma_load_3d(st + PR_TILE_BYTES, occ ? b_occ : b_vir, &full[stage], x, b_row, t);
+                issued[stage] = 1;
+                issued_phase[stage] = phase;
+                if (++stage == PR_STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+                return true;
+            });
             if (!ok)
                 for (int s = 0; s < PR_STAGES; ++s)
                     if (issued[s]) mbar_drain(&full[s], issued_phase[s], args.timeout_ns);
@@ -966,7 +992,6 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             int stage = 0;
             uint32_t phase = 0;
             uint32_t use[PR_GROUPS] = {0, 0};  // parity of each group's uses so far
-            bool ok = true;
             const uint32_t id = idesc_pair(TF32 ? idesc_tf32(256, false) : idesc_bf16(256, false));
             constexpr uint16_t BOTH = 3;
             // Descriptors of stage 0; stage s adds s * PR_STAGE_BYTES to the start-address
@@ -978,60 +1003,50 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             constexpr uint32_t BOFF = PR_TILE_BYTES;
             const uint64_t brh0 = sdesc_sw128(base0 + BOFF + 0), brl0 = sdesc_sw128(base0 + BOFF + 32);
             const uint64_t bih0 = sdesc_sw128(base0 + BOFF + 64), bil0 = sdesc_sw128(base0 + BOFF + 96);
-            int li = 0;
-            for (int item = cid; item < n_items && ok; item += ncl, ++li) {
+            for_each_chunk(cid, ncl, n_items, n_occ_chunks, n_vir_chunks, [&](int li, int, bool occ, int c) {
                 const int g = li & 1;
                 const uint32_t d = tmem + 256u * g;  // [Re G | Im G]
-                if (!mbar_wait_fast(&pfree[g], use[g] ^ 1u, args.abort_flag, 2, args.timeout_ns)) {
-                    ok = false;
-                    break;
-                }
-                fence_after();
-                for (int c = 0; c < stages_per_tile; ++c) {
-                    if (c == n_occ_stages) {
-                        // G- complete: hand it to both CTAs' groups, then reuse the columns for G+.
-                        umma_pair_commit(&mfull[g], BOTH);
-                        if (!mbar_wait_fast(&munl[g], use[g], args.abort_flag, 5, args.timeout_ns)) {
-                            ok = false;
-                            break;
-                        }
-                        fence_after();
-                    }
-                    if (!mbar_wait_fast(&full[stage], phase, args.abort_flag, 3, args.timeout_ns)) {
-                        ok = false;
-                        break;
-                    }
+                if (c == 0) {
+                    // G-: the group has traced its previous item; G+: it has unloaded this item's G-.
+                    const bool ready = occ ? mbar_wait_fast(&pfree[g], use[g] ^ 1u, args.abort_flag, 2, args.timeout_ns)
+                                           : mbar_wait_fast(&munl[g], use[g], args.abort_flag, 5, args.timeout_ns);
+                    if (!ready) return false;
                     fence_after();
-                    const uint64_t so = (uint64_t)(stage * (PR_STAGE_BYTES >> 4));
-                    const uint64_t arh = arh0 + so, arl = arl0 + so, aih = aih0 + so, ail = ail0 + so;
-                    const uint64_t brh = brh0 + so, brl = brl0 + so, bih = bih0 + so, bil = bil0 + so;
-                    const uint32_t acc = (c == 0 || c == n_occ_stages) ? 0u : 1u;
-                    // [Re | Im] += X_re [Y; iY]_re^T + X_im [Y; iY]_im^T (straight-line code:
-                    // the issue loop must stay short, the tensor pipe drains while it runs).
-                    if constexpr (TF32) {
-                        // descriptors at +0, +32, +64, +96: re K 0-7, re K 8-15, im K 0-7, im K 8-15
-                        umma_pair_tf32(d, arh, brh, id, acc);
-                        umma_pair_tf32(d, arl, brl, id, 1u);
-                        umma_pair_tf32(d, aih, bih, id, 1u);
-                        umma_pair_tf32(d, ail, bil, id, 1u);
-                    } else {
-                        umma_pair(d, arh, brh, id, acc);
-                        umma_pair(d, arh, brl, id, 1u);
-                        umma_pair(d, arl, brh, id, 1u);
-                        umma_pair(d, aih, bih, id, 1u);
-                        umma_pair(d, aih, bil, id, 1u);
-                        umma_pair(d, ail, bih, id, 1u);
-                    }
-                    umma_pair_commit(&empty[stage], BOTH);
-                    if (++stage == PR_STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
                 }
-                if (!ok) break;
-                umma_pair_commit(&pfull[g], BOTH);
-                use[g] ^= 1u;
-            }
+                if (!mbar_wait_fast(&full[stage], phase, args.abort_flag, 3, args.timeout_ns)) return false;
+                fence_after();
+                const uint64_t so = (uint64_t)(stage * (PR_STAGE_BYTES >> 4));
+                const uint64_t arh = arh0 + so, arl = arl0 + so, aih = aih0 + so, ail = ail0 + so;
+                const uint64_t brh = brh0 + so, brl = brl0 + so, bih = bih0 + so, bil = bil0 + so;
+                const uint32_t acc = c == 0 ? 0u : 1u;
+                // [Re | Im] += X_re [Y; iY]_re^T + X_im [Y; iY]_im^T (straight-line code:
+                // the issue loop must stay short, the tensor pipe drains while it runs).
+                if constexpr (TF32) {
+                    // descriptors at +0, +32, +64, +96: re K 0-7, re K 8-15, im K 0-7, im K 8-15
+                    umma_pair_tf32(d, arh, brh, id, acc);
+                    umma_pair_tf32(d, arl, brl, id, 1u);
+                    umma_pair_tf32(d, aih, bih, id, 1u);
+                    umma_pair_tf32(d, ail, bil, id, 1u);
+                } else {
+                    umma_pair(d, arh, brh, id, acc);
+                    umma_pair(d, arh, brl, id, 1u);
+                    umma_pair(d, arl, brh, id, 1u);
+                    umma_pair(d, aih, bih, id, 1u);
+                    umma_pair(d, aih, bil, id, 1u);
+                    umma_pair(d, ail, bih, id, 1u);
+                }
+                umma_pair_commit(&empty[stage], BOTH);
+                if (++stage == PR_STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+                if (occ && c == n_occ_chunks - 1) umma_pair_commit(&mfull[g], BOTH);  // G- to both CTAs' group
+                if (!occ && c == n_vir_chunks - 1) {                               // G+ complete
+                    umma_pair_commit(&pfull[g], BOTH);
+                    use[g] ^= 1u;
+                }
+                return true;
+            });
             // Let every MMA this thread issued finish before tensor memory is freed.
             umma_pair_commit(&empty[stage], 1);
             mbar_drain(&empty[stage], phase, args.timeout_ns);
