@@ -21,7 +21,8 @@ import math
 import time
 
 
-def run(units, m=4096, n_tau=8, burn=200, steps=400, timed=20, precision="mixed", seed=2203, target=1e-3):
+def run(units, m=4096, n_tau=8, burn=200, steps=400, timed=20, precision="mixed", seed=2203, target=1e-3,
+        soft=False):
     import numpy as np
     import torch
 
@@ -31,7 +32,7 @@ def run(units, m=4096, n_tau=8, burn=200, steps=400, timed=20, precision="mixed"
     prec = pkg.MCMP2_MIXED if precision == "mixed" else pkg.MCMP2_FP64
     rows = []
     for n in units:
-        system = synthetic.make_system("size", seed=seed, n_units=n)
+        system = synthetic.make_system("size", seed=seed, n_units=n, soft=soft)
         ctx = pkg.Context(system, m, n_tau, prec)
         ctx.set_walkers(None, seed + n, burn)
         ctx.run_steps(3, seed + n)
@@ -77,8 +78,8 @@ def run(units, m=4096, n_tau=8, burn=200, steps=400, timed=20, precision="mixed"
         "time_to_target_vs_electrons": fit("time_to_target_s", "n_electrons"),
         "time_to_target_vs_basis": fit("time_to_target_s", "n_basis"),
     }
-    return {"m": m, "n_tau": n_tau, "precision": precision, "target_relative_error": target, "rows": rows,
-            "exponents": fits}
+    return {"m": m, "n_tau": n_tau, "precision": precision, "soft": soft, "target_relative_error": target,
+            "rows": rows, "exponents": fits}
 
 
 def main():
@@ -89,8 +90,11 @@ def main():
     ap.add_argument("--burn", type=int, default=200)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--soft", action="store_true",
+                    help="soft units (exponents and energies inside the weight function's reach): finite variance")
     args = ap.parse_args()
-    out = run(args.units, m=args.m, n_tau=args.n_tau, burn=args.burn, steps=args.steps, precision=args.precision)
+    out = run(args.units, m=args.m, n_tau=args.n_tau, burn=args.burn, steps=args.steps, precision=args.precision,
+              soft=args.soft)
     print(json.dumps(out))
 
 

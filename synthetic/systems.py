@@ -266,6 +266,10 @@ _SOFT_H = [(0, 0.08, 2.5, 3)]                                        # 3
 # the weight function and the estimator has a finite variance.
 _SOFT_SN = [(0, 0.05, 1.4, 14), (1, 0.08, 1.4, 8), (2, 0.2, 1.4, 3)]
 _SOFT_CL = [(0, 0.05, 1.4, 8), (1, 0.08, 1.4, 6), (2, 0.2, 1.4, 2)]
+# Soft variant of the size-series units (Z=80 + 2 Z=17, 110 functions per unit),
+# ratio 1.3 (largest exponent 5.1).
+_SOFT_HG = [(0, 0.1, 1.3, 16), (1, 0.1, 1.3, 8), (2, 0.2, 1.3, 4)]
+_SOFT_SIZE_CL = [(0, 0.1, 1.3, 8), (1, 0.1, 1.3, 5)]
 
 
 def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = False,
@@ -291,8 +295,11 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     for ic, z in enumerate(charges):
         recipe = _recipe(config, z)
         if soft:
-            assert config in ("tiny", "medium"), "soft variants exist for the tiny and medium systems"
-            recipe = {30: _SOFT_ZN, 1: _SOFT_H, 50: _SOFT_SN, 17: _SOFT_CL}[z]
+            assert config in ("tiny", "medium", "size"), "soft variants exist for the tiny, medium and size systems"
+            if config == "size":
+                recipe = {80: _SOFT_HG, 17: _SOFT_SIZE_CL}[z]
+            else:
+                recipe = {30: _SOFT_ZN, 1: _SOFT_H, 50: _SOFT_SN, 17: _SOFT_CL}[z]
         shells += _shells_for(ic, recipe)
     shell_centre = np.array([s[0] for s in shells], dtype=np.int32)
     shell_l = np.array([s[1] for s in shells], dtype=np.int32)

@@ -28,3 +28,15 @@ def test_generators_are_seeded():
     b = synthetic.make_system("medium", soft=True)
     assert a.digest() == b.digest()
     assert synthetic.make_system("medium", soft=True, seed=7).digest() != a.digest()
+
+
+def test_soft_size_units_keep_the_unit_sizes():
+    for n in (1, 2):
+        lit = synthetic.make_system("size", n_units=n)
+        soft = synthetic.make_system("size", n_units=n, soft=True)
+        assert soft.n_l == lit.n_l == 110 * n
+        assert (soft.n_occ, soft.n_vir) == (lit.n_occ, lit.n_vir) == (40 * n, 180 * n)
+        assert soft.shell_alpha.max() < 6.0 < lit.shell_alpha.max()
+        assert soft.eps[:soft.n_occ].min() >= -2.0 and soft.eps[soft.n_occ:].max() <= 3.0
+        # the weight function's most diffuse Gaussian lies inside 4x the most diffuse basis exponent
+        assert soft.weight[:, [1, 3]].min() < 4.0 * soft.shell_alpha.min()
