@@ -24,10 +24,10 @@ def test_medium_and_soft_medium_share_the_workload_sizes():
 
 
 def test_generators_are_seeded():
-    a = synthetic.make_system("medium", soft=True)
-    b = synthetic.make_system("medium", soft=True)
-    assert a.digest() == b.digest()
-    assert synthetic.make_system("medium", soft=True, seed=7).digest() != a.digest()
+    for kw in ({"config": "tiny"}, {"config": "size", "soft": True}):
+        a = synthetic.make_system(**kw)
+        assert a.digest() == synthetic.make_system(**kw).digest()
+        assert synthetic.make_system(seed=7, **kw).digest() != a.digest()
 
 
 def test_soft_size_units_keep_the_unit_sizes():
