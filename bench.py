@@ -41,7 +41,7 @@ TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 # DRAM bytes (read + write) of one contraction launch at m = 1024, 4 tau, from
 # the ncu captures summarised in profiles/pairs_mixed_{bf16x3,tf32}_medium_m1024.md
 # (the kernels as they stand; None where no capture of the current kernel exists).
-PAIRS_TRAFFIC_BYTES = {"mixed": 297.3e6, "tf32": 297.6e6}
+PAIRS_TRAFFIC_BYTES = {"mixed": 298.3e6, "tf32": 297.2e6}
 
 
 def flops_per_sample(n_occ, n_vir, n_comp=4):
