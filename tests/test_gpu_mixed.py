@@ -184,3 +184,29 @@ def test_size_series_launch_sampled_tiles(prec):
             for t in range(n_tau):
                 bound = 8.0 * U_TF32 * _abs_expansion_sum(orc, system, r[0], tau[0][t:t + 1], pairs)[0]
                 assert abs(got[t] - want[t]) <= bound, (bp, bq, t, got[t], want[t], bound)
+
+
+@pytest.mark.parametrize("prec", [pkg.MCMP2_FP64, pkg.MCMP2_MIXED])
+def test_odd_basis_count(tiny, prec):
+    """A basis with an odd number of functions (the tiny system without its last s
+    shell, n_L = 19): the basis kernels' paired stores fall back to single values."""
+    import dataclasses
+    n_l = tiny.n_l
+    keep = np.ones(len(tiny.shell_l), dtype=bool)
+    keep[-1] = False
+    assert tiny.shell_l[-1] == 0
+    rows = np.concatenate([np.arange(k * n_l, (k + 1) * n_l - 1) for k in range(4)])
+    odd = dataclasses.replace(tiny, shell_centre=tiny.shell_centre[keep], shell_l=tiny.shell_l[keep],
+                              shell_alpha=tiny.shell_alpha[keep], shell_coef=tiny.shell_coef[keep],
+                              C=np.ascontiguousarray(tiny.C[rows]))
+    assert odd.n_l == 19
+    orc = oracle.Oracle(odd)
+    m, n_tau = 16, 2
+    r = synthetic.walker_positions(odd.centres, 2, m, seed=91)
+    tau = synthetic.imaginary_times(orc.lam(), 2, n_tau, seed=92)
+    got = pkg.Context(odd, m, n_tau, prec).eval_fixed(r, tau)
+    want, absmean = orc.eval_steps(r, tau, with_abs=True)
+    if prec == pkg.MCMP2_FP64:
+        assert np.all(np.abs(got - want) <= 1e-10 * np.maximum(np.abs(want), 1e-3 * absmean)), (got, want)
+    else:
+        assert np.all(_ok(got, want, absmean)), (got, want)
