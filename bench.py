@@ -38,10 +38,11 @@ WORKLOAD = ("medium: 6 centres (4 x Z=50, 2 x Z=17), n_L=300 (+600 small), 80 oc
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 CUDA-core FP64 (no FP64 tensor path on this part)
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
-# DRAM bytes (read + write) of one contraction launch at m = 1024, 4 tau, from
-# the ncu captures summarised in profiles/pairs_mixed_{bf16x3,tf32}_medium_m1024.md
-# (the kernels as they stand; None where no capture of the current kernel exists).
-PAIRS_TRAFFIC_BYTES = {"mixed": 298.3e6, "tf32": 297.2e6}
+# DRAM bytes (read + write) of one contraction launch at m = 1024, 4 tau, keyed
+# by (form, spinor components), from the ncu captures summarised in
+# profiles/pairs_mixed_{bf16x3,tf32,bf16x3_2c}_medium_m1024.md (the kernels as
+# they stand; None where no capture of the current kernel exists).
+PAIRS_TRAFFIC_BYTES = {("mixed", 4): 298.3e6, ("tf32", 4): 297.2e6, ("mixed", 2): 137.5e6}
 
 
 def flops_per_sample(n_occ, n_vir, n_comp=4):
@@ -376,7 +377,7 @@ def main():
         peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
         issued = achieved * issued_per_algorithmic(system.n_occ, system.n_vir, 3, args.components)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES["mixed"] if m_run == M and not two_c else None,
+                "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES.get(("mixed", args.components)) if m_run == M else None,
                 "peak_kind": f"{peak_kind} bf16 sustained",
                 "issued": {"tflops": issued, "frac": issued / peak,
                            "note": "BF16 tensor work actually issued: 3 split products, full 128 x 128 tiles"}}
@@ -384,7 +385,7 @@ def main():
         peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]) * TF32_OVER_BF16
         issued = achieved * issued_per_algorithmic(system.n_occ, system.n_vir, 1, args.components)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES["tf32"] if m_run == M and not two_c else None,
+                "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES.get(("tf32", args.components)) if m_run == M else None,
                 "peak_kind": f"{peak_kind} bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)",
                 "issued": {"tflops": issued, "frac": issued / peak,
                            "note": "TF32 tensor work actually issued: full 128 x 128 tiles"}}
