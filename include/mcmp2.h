@@ -124,9 +124,11 @@ int mcmp2_create(mcmp2_ctx **ctx, int device, void *cuda_stream, int precision);
  * MCMP2_GAUNT or MCMP2_BREIT) for the following steps and replays.  Each electron pair's
  * interaction (1/r_ab) sum_A c_A O_A(a) O_A(b), O_A in {1, alpha_x, alpha_y, alpha_z,
  * alpha.n_ab}, enters the trace form with O_A at the two points of the pair (the
- * weight's 1/r_ab is unchanged).  FP64 form only: MCMP2_EUNSUPPORTED in the tensor-core
- * forms for anything but MCMP2_COULOMB; mcmp2_backward requires MCMP2_COULOMB.
- * Statistics accumulated so far are kept; checkpoints record the interaction. */
+ * weight's 1/r_ab is unchanged).  All three precisions (the tensor-core forms apply
+ * the operators to the G- blocks in their trace epilogue); four-component systems
+ * only (MCMP2_EUNSUPPORTED after mcmp2_load_system_2c); mcmp2_backward requires
+ * MCMP2_COULOMB.  Statistics accumulated so far are kept; checkpoints record the
+ * interaction. */
 int mcmp2_set_interaction(mcmp2_ctx *ctx, int interaction);
 
 /* Release the context (not the caller's workspace).  NULL is ignored. */

@@ -465,6 +465,7 @@ struct PairArgs {
     double inv_lambda;
     unsigned long long timeout_ns;  // limit of every wait
     int withhold_first_copy;        // test hook: never issue the first stage's copy (its wait runs out)
+    const double *r = nullptr;      // walker positions [m][2][3] (the Breit terms' unit vectors)
 };
 
 // Pair tile k -> (BP, bq): row BP of the enumeration holds bq = 2 BP .. nb - 1.
@@ -551,8 +552,245 @@ struct EpiCtx {
     uint32_t munl_even, pfree_even;
 };
 
+// ---------------------------------------------------------------------------
+// Gaunt and Breit terms (Sec. II: g_ab = (1/r_ab) sum_A c_A O_A(a) O_A(b) with
+// O in {1, alpha_x, alpha_y, alpha_z, alpha.n_ab}, c = 1, -1/2, -1/2, -1/2, -1/2).
+// With O_A at the points of pair p and O_B at those of pair q, both traces of
+// the trace form keep their Coulomb shape once G- is replaced by
+// M_AB = O_A G- O_B (the operators are Hermitian):
+//   direct   T_AB(x, y) = sum_cd conj(M_AB(x, y)_cd) G+(x, y)_cd, D = sum c_A c_B T_AB(1p,1q) T_AB(2p,2q),
+//   exchange tr[M_AB(1p,1q)^dag G+(1p,2q) M_AB(2p,2q)^dag G+(2p,1q)].
+// alpha_k has sigma_k in its off-diagonal 2x2 blocks (components L-alpha,
+// L-beta, S-alpha, S-beta), so O_A = alpha_k maps row c of G- to row c^3
+// (x, y) or c^2 (z) times a phase rho_k(c), and O_B permutes the columns the
+// same way; alpha.n is the combination sum_k n_k alpha_k.
+// ---------------------------------------------------------------------------
+
+// Row r (of 128) of the parked G- block of q-pair ql: four complex entries.
+__device__ __forceinline__ void gm_row(const unsigned char *gm, int ql, int r, float *re, float *im)
+{
+    const uint2 *gp = reinterpret_cast<const uint2 *>(gm);
+    const uint2 w0 = gp[(3 * ql + 0) * 128 + r];
+    const uint2 w1 = gp[(3 * ql + 1) * 128 + r];
+    const uint2 w2 = gp[(3 * ql + 2) * 128 + r];
+    unpack24(w0.x, w0.y, w1.x, re[0], im[0], re[1], im[1]);
+    unpack24(w1.y, w2.x, w2.y, re[2], im[2], re[3], im[3]);
+}
+
+// h_B = sum_d conj((R O_B)_d) Y_d for O_B = 1, alpha_x, alpha_y, alpha_z, where
+// (R alpha_x)_d = R_{d^3}, (R alpha_y)_d = kappa_d R_{d^3} (kappa = i for even d,
+// -i for odd d) and (R alpha_z)_d = +-R_{d^2} (+ for even d).  The even- and
+// odd-d halves of the two permuted dot products give all four.
+__device__ __forceinline__ void row_dots(const float *Rr, const float *Ri, const float *Yr, const float *Yi, float *hr,
+                                         float *hi)
+{
+    float fr = 0.f, fi = 0.f;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        fr += Rr[d] * Yr[d] + Ri[d] * Yi[d];
+        fi += Rr[d] * Yi[d] - Ri[d] * Yr[d];
+    }
+    const float exr = Rr[3] * Yr[0] + Ri[3] * Yi[0] + Rr[1] * Yr[2] + Ri[1] * Yi[2];
+    const float exi = Rr[3] * Yi[0] - Ri[3] * Yr[0] + Rr[1] * Yi[2] - Ri[1] * Yr[2];
+    const float oxr = Rr[2] * Yr[1] + Ri[2] * Yi[1] + Rr[0] * Yr[3] + Ri[0] * Yi[3];
+    const float oxi = Rr[2] * Yi[1] - Ri[2] * Yr[1] + Rr[0] * Yi[3] - Ri[0] * Yr[3];
+    const float ezr = Rr[2] * Yr[0] + Ri[2] * Yi[0] + Rr[0] * Yr[2] + Ri[0] * Yi[2];
+    const float ezi = Rr[2] * Yi[0] - Ri[2] * Yr[0] + Rr[0] * Yi[2] - Ri[0] * Yr[2];
+    const float ozr = Rr[3] * Yr[1] + Ri[3] * Yi[1] + Rr[1] * Yr[3] + Ri[1] * Yi[3];
+    const float ozi = Rr[3] * Yi[1] - Ri[3] * Yr[1] + Rr[1] * Yi[3] - Ri[1] * Yr[3];
+    hr[0] = fr;
+    hi[0] = fi;
+    hr[1] = exr + oxr;
+    hi[1] = exi + oxi;
+    hr[2] = exi - oxi;  // i (ox - ex)
+    hi[2] = oxr - exr;
+    hr[3] = ezr - ozr;
+    hi[3] = ezi - ozi;
+}
+
+// sum_B c_B Re(G_B H_B) over B = 0, x, y, z (and n = alpha.n_q with BREIT).
+template <bool BREIT>
+__device__ __forceinline__ float re_prod_sum(const float *Gr, const float *Gi, const float *Hr, const float *Hi,
+                                             float nqx, float nqy, float nqz)
+{
+    float s = Gr[0] * Hr[0] - Gi[0] * Hi[0];
+    float t = 0.f;
+#pragma unroll
+    for (int B = 1; B < 4; ++B) t += Gr[B] * Hr[B] - Gi[B] * Hi[B];
+    if constexpr (BREIT) {
+        const float gr = nqx * Gr[1] + nqy * Gr[2] + nqz * Gr[3], gi = nqx * Gi[1] + nqy * Gi[2] + nqz * Gi[3];
+        const float hr = nqx * Hr[1] + nqy * Hr[2] + nqz * Hr[3], hi = nqx * Hi[1] + nqy * Hi[2] + nqz * Hi[3];
+        t += gr * hr - gi * hi;
+    }
+    return s - 0.5f * t;
+}
+
+// This lane's share of direct - exchange for one pair of pairs with the Gaunt
+// (BREIT = false) or Breit terms.  Lane (e, c) holds row c of G+(xe, ye) (dia) and
+// G+(xe, y(1-e)) (off); the G- rows come from shared memory (own0: rows of its
+// electron's block, par0: the other electron's).  The eight lanes' shares sum
+// to D - X.
+template <bool BREIT>
+__device__ __forceinline__ float terms_part(const unsigned char *gm, int ql, int own0, int par0, int e, int c,
+                                            int lane, const float *dia_r, const float *dia_i, const float *off_r,
+                                            const float *off_i, float npx, float npy, float npz, float nqx,
+                                            float nqy, float nqz)
+{
+    const float sc = (c & 1) ? -1.f : 1.f;  // rho_y(c) = -i sc, rho_z(c) = sc
+    float Rr[4], Ri[4];
+    // (a) exchange: as in the Coulomb trace, lane (e, c) pairs its rows with the
+    //     other electron's rows c'' (two per lane), now for every (A, B).
+    float xl = 0.f;
+    const int gbase = lane & ~7;
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        const int cpp = e == 0 ? ((c + s) & 3) : ((c + 2 - s) & 3);
+        const int src = gbase + 4 * (1 - e) + cpp;
+        const float sp = (cpp & 1) ? -1.f : 1.f;
+        float ror[4], roi[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            ror[d] = __shfl_sync(0xffffffffu, off_r[d], src);
+            roi[d] = __shfl_sync(0xffffffffu, off_i[d], src);
+        }
+        float Hr[4], Hi[4], Gr[4], Gi[4];
+        // A = 0
+        gm_row(gm, ql, own0 + c, Rr, Ri);
+        row_dots(Rr, Ri, ror, roi, Hr, Hi);
+        gm_row(gm, ql, par0 + cpp, Rr, Ri);
+        row_dots(Rr, Ri, off_r, off_i, Gr, Gi);
+        xl += re_prod_sum<BREIT>(Gr, Gi, Hr, Hi, nqx, nqy, nqz);
+        // A = x, y share rows c^3 and c''^3: products 1 and -sc sp
+        float H3r[4], H3i[4], G3r[4], G3i[4];
+        gm_row(gm, ql, own0 + (c ^ 3), Rr, Ri);
+        row_dots(Rr, Ri, ror, roi, H3r, H3i);
+        gm_row(gm, ql, par0 + (cpp ^ 3), Rr, Ri);
+        row_dots(Rr, Ri, off_r, off_i, G3r, G3i);
+        xl -= 0.5f * (1.f - sc * sp) * re_prod_sum<BREIT>(G3r, G3i, H3r, H3i, nqx, nqy, nqz);
+        // A = z: rows c^2 and c''^2, product sc sp
+        gm_row(gm, ql, own0 + (c ^ 2), Rr, Ri);
+        row_dots(Rr, Ri, ror, roi, Hr, Hi);
+        gm_row(gm, ql, par0 + (cpp ^ 2), Rr, Ri);
+        row_dots(Rr, Ri, off_r, off_i, Gr, Gi);
+        xl -= 0.5f * sc * sp * re_prod_sum<BREIT>(Gr, Gi, Hr, Hi, nqx, nqy, nqz);
+        if constexpr (BREIT) {
+            // A = alpha.n_p: (nx + i ny sgn) row^3 + nz sgn row^2 on each side, B = 0, x, y, z, n.
+            float s0 = 0.f, t = 0.f, anr = 0.f, ani = 0.f, bnr = 0.f, bni = 0.f;
+#pragma unroll
+            for (int B = 0; B < 4; ++B) {
+                const float ar = npx * G3r[B] - npy * sp * G3i[B] + npz * sp * Gr[B];
+                const float ai = npx * G3i[B] + npy * sp * G3r[B] + npz * sp * Gi[B];
+                const float br = npx * H3r[B] - npy * sc * H3i[B] + npz * sc * Hr[B];
+                const float bi = npx * H3i[B] + npy * sc * H3r[B] + npz * sc * Hi[B];
+                if (B == 0) {
+                    s0 = ar * br - ai * bi;
+                } else {
+                    const float wq = B == 1 ? nqx : (B == 2 ? nqy : nqz);
+                    t += ar * br - ai * bi;
+                    anr += wq * ar;
+                    ani += wq * ai;
+                    bnr += wq * br;
+                    bni += wq * bi;
+                }
+            }
+            t += anr * bnr - ani * bni;
+            xl -= 0.5f * (s0 - 0.5f * t);
+        }
+    }
+    // (b) direct: lane partials t_AB, slot k = 4A + B (re, im); with BREIT also
+    //     t_nB (B = 0, x, y, z, n) for O_A = alpha.n_p.
+    float v[32];
+    float tn[10];
+    {
+        float H0r[4], H0i[4], H3r[4], H3i[4], H2r[4], H2i[4];
+        gm_row(gm, ql, own0 + c, Rr, Ri);
+        row_dots(Rr, Ri, dia_r, dia_i, H0r, H0i);
+        gm_row(gm, ql, own0 + (c ^ 3), Rr, Ri);
+        row_dots(Rr, Ri, dia_r, dia_i, H3r, H3i);
+        gm_row(gm, ql, own0 + (c ^ 2), Rr, Ri);
+        row_dots(Rr, Ri, dia_r, dia_i, H2r, H2i);
+#pragma unroll
+        for (int B = 0; B < 4; ++B) {
+            v[2 * B] = H0r[B];
+            v[2 * B + 1] = H0i[B];
+            v[2 * (4 + B)] = H3r[B];
+            v[2 * (4 + B) + 1] = H3i[B];
+            v[2 * (8 + B)] = -sc * H3i[B];  // conj(rho_y(c)) = i sc
+            v[2 * (8 + B) + 1] = sc * H3r[B];
+            v[2 * (12 + B)] = sc * H2r[B];
+            v[2 * (12 + B) + 1] = sc * H2i[B];
+        }
+    }
+    if constexpr (BREIT) {
+        // t_nB = sum_k n_p,k t_kB (the operator enters linearly), then B = alpha.n_q likewise.
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tn[j] = npx * v[8 + j] + npy * v[16 + j] + npz * v[24 + j];
+        tn[8] = nqx * tn[2] + nqy * tn[4] + nqz * tn[6];
+        tn[9] = nqx * tn[3] + nqy * tn[5] + nqz * tn[7];
+    }
+    // Sum over the four lanes c of the electron by halving exchanges: after them
+    // lane c holds T_AB for A = 2 (c & 1) + (c >> 1) and B = 0..3.
+    const bool h1 = lane & 1, h2 = lane & 2;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float send = h1 ? v[j] : v[j + 16];
+        const float keep = h1 ? v[j + 16] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float send = h2 ? v[j] : v[j + 8];
+        const float keep = h2 ? v[j + 8] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    float w[8];  // the same T_AB of the other electron
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = __shfl_xor_sync(0xffffffffu, v[j], 4);
+    const float cA = ((lane & 3) == 0) ? 1.f : -0.5f;  // A = 0 on lane c = 0 only
+    float dl;
+    {
+        float vr[4], vi[4], wr[4], wi[4];
+#pragma unroll
+        for (int B = 0; B < 4; ++B) {
+            vr[B] = v[2 * B];
+            vi[B] = v[2 * B + 1];
+            wr[B] = w[2 * B];
+            wi[B] = w[2 * B + 1];
+        }
+        dl = cA * re_prod_sum<BREIT>(vr, vi, wr, wi, nqx, nqy, nqz);
+    }
+    if constexpr (BREIT) {
+        // The alpha.n_p row, summed over all four lanes (each then holds it: count a quarter).
+#pragma unroll
+        for (int j = 0; j < 10; ++j) tn[j] += __shfl_xor_sync(0xffffffffu, tn[j], 1);
+#pragma unroll
+        for (int j = 0; j < 10; ++j) tn[j] += __shfl_xor_sync(0xffffffffu, tn[j], 2);
+        float nr = 0.f;
+#pragma unroll
+        for (int B = 0; B < 5; ++B) {
+            const float ur = __shfl_xor_sync(0xffffffffu, tn[2 * B], 4);
+            const float ui = __shfl_xor_sync(0xffffffffu, tn[2 * B + 1], 4);
+            nr += (B == 0 ? 1.f : -0.5f) * (tn[2 * B] * ur - tn[2 * B + 1] * ui);
+        }
+        dl -= 0.125f * nr;  // c_n = -1/2, a quarter
+    }
+    dl *= 0.5f;  // both electrons' lanes hold each product
+    return dl - xl;
+}
+
+__device__ __forceinline__ void unit_pair_vector(const double *r, int p, float &x, float &y, float &z)
+{
+    const double dx = r[6 * p] - r[6 * p + 3], dy = r[6 * p + 1] - r[6 * p + 4], dz = r[6 * p + 2] - r[6 * p + 5];
+    const double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+    x = (float)(dx * inv);
+    y = (float)(dy * inv);
+    z = (float)(dz * inv);
+}
+
 // Trace epilogue of a four-component tile: rows 8p + 4e + c of 16 p-pairs,
 // columns 8q + 4e' + d of 16 q-pairs; the eight lanes (e, c) of a pair hold its rows.
+// INTER: MCMP2_COULOMB, MCMP2_GAUNT or MCMP2_BREIT.
+template <int INTER>
 __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned char *smem, uint32_t tmem,
                                                   int warp, int lane, const EpiCtx &ec, uint64_t *mfull,
                                                   uint64_t *pfull)
@@ -616,9 +854,46 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
         // a_q of the tile's 16 q-pairs, one per lane (lane & 15), fetched by shuffle below.
         const int q_lane = bq * 16 + (lane & 15);
         const double a_lane = q_lane < args.m ? args.a[q_lane] : 0.0;
+        // Breit: unit vectors n = (r1 - r2) / r12 of this lane's p-pair and of q-pair q_lane.
+        float npx = 0.f, npy = 0.f, npz = 0.f, nlx = 0.f, nly = 0.f, nlz = 0.f;
+        if constexpr (INTER == MCMP2_BREIT) {
+            if (p < args.m) unit_pair_vector(args.r, p, npx, npy, npz);
+            if (q_lane < args.m) unit_pair_vector(args.r, q_lane, nlx, nly, nlz);
+        }
         double acc = 0.0;  // sum over this warp's q of Re f_pq a_q
+        if constexpr (INTER != MCMP2_COULOMB) {
+            // One q-pair per tensor-memory load: the operator terms hold more state per q.
 #pragma unroll 1
-        for (int qb = 0; qb < 4; ++qb) {
+            for (int qi = 0; qi < 8; ++qi) {
+                const int ql = 8 * qhalf + qi;
+                float gpr[8], gpi[8];
+                tmem_ld<8>(lane_addr + 8u * ql, gpr);
+                tmem_ld<8>(lane_addr + 128u + 8u * ql, gpi);
+                tmem_wait_ld();
+                float dia_r[4], dia_i[4], off_r[4], off_i[4];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    dia_r[d] = e ? gpr[4 + d] : gpr[d];
+                    dia_i[d] = e ? gpi[4 + d] : gpi[d];
+                    off_r[d] = e ? gpr[d] : gpr[4 + d];
+                    off_i[d] = e ? gpi[d] : gpi[4 + d];
+                }
+                const int q = bq * 16 + ql;
+                const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
+                const float nqx = __shfl_sync(0xffffffffu, nlx, ql);
+                const float nqy = __shfl_sync(0xffffffffu, nly, ql);
+                const float nqz = __shfl_sync(0xffffffffu, nlz, ql);
+                float part = terms_part<INTER == MCMP2_BREIT>(gm, ql, row & ~3, (row ^ 4) & ~3, e, c, lane, dia_r,
+                                                              dia_i, off_r, off_i, npx, npy, npz, nqx, nqy, nqz);
+                part += __shfl_xor_sync(0xffffffffu, part, 1);
+                part += __shfl_xor_sync(0xffffffffu, part, 2);
+                part += __shfl_xor_sync(0xffffffffu, part, 4);
+                const bool valid = p < args.m && q < args.m && (bp < bq || (bp == bq && p_local < ql));
+                if (valid) acc += (double)(-0.5f * part) * a_q;
+            }
+        }
+#pragma unroll 1
+        for (int qb = 0; qb < (INTER == MCMP2_COULOMB ? 4 : 0); ++qb) {
             const int q0 = 8 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
             float gpr[16], gpi[16];
             tmem_ld<16>(lane_addr + 8u * q0, gpr);
@@ -628,15 +903,6 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
             for (int qq = 0; qq < 2; ++qq) {
                 // This lane holds row c of G-(xe, ye) [own], G+(xe, ye) [dia], G+(xe, y(1-e)) [off].
                 const int ql = q0 + qq;
-                float own_r[4], own_i[4];
-                {
-                    const uint2 *gp = reinterpret_cast<const uint2 *>(gm);
-                    const uint2 w0 = gp[(3 * ql + 0) * 128 + row];
-                    const uint2 w1 = gp[(3 * ql + 1) * 128 + row];
-                    const uint2 w2 = gp[(3 * ql + 2) * 128 + row];
-                    unpack24(w0.x, w0.y, w1.x, own_r[0], own_i[0], own_r[1], own_i[1]);
-                    unpack24(w1.y, w2.x, w2.y, own_r[2], own_i[2], own_r[3], own_i[3]);
-                }
                 float dia_r[4], dia_i[4], off_r[4], off_i[4];
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {  // constant indices keep the arrays in registers
@@ -645,6 +911,15 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
                     dia_i[d] = e ? gpi[i1] : gpi[i0];
                     off_r[d] = e ? gpr[i0] : gpr[i1];
                     off_i[d] = e ? gpi[i0] : gpi[i1];
+                }
+                float own_r[4], own_i[4];
+                {
+                    const uint2 *gp = reinterpret_cast<const uint2 *>(gm);
+                    const uint2 w0 = gp[(3 * ql + 0) * 128 + row];
+                    const uint2 w1 = gp[(3 * ql + 1) * 128 + row];
+                    const uint2 w2 = gp[(3 * ql + 2) * 128 + row];
+                    unpack24(w0.x, w0.y, w1.x, own_r[0], own_i[0], own_r[1], own_i[1]);
+                    unpack24(w1.y, w2.x, w2.y, own_r[2], own_i[2], own_r[3], own_i[3]);
                 }
                 // Direct: T_e = sum_cd conj(G-_cd) G+_cd over the like-electron block.
                 float tr = 0.f, ti = 0.f;
@@ -870,7 +1145,7 @@ __device__ __forceinline__ bool for_each_chunk(int cid, int ncl, int n_items, in
     return true;
 }
 
-template <bool TF32, int NC>
+template <bool TF32, int NC, int INTER = MCMP2_COULOMB>
 __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid_constant__ PairMaps maps,
                                                                     const PairArgs args)
 {
@@ -1058,7 +1333,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
         if constexpr (NC == 2)
             pairs_epilogue_2c(args, smem, tmem, warp, lane, ec, mfull, pfull);
         else
-            pairs_epilogue_4c(args, smem, tmem, warp, lane, ec, mfull, pfull);
+            pairs_epilogue_4c<INTER>(args, smem, tmem, warp, lane, ec, mfull, pfull);
     }
     fence_before();
     __syncthreads();
@@ -1256,7 +1531,15 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
         cudaFuncSetAttribute(pairs_mixed_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
             cudaSuccess ||
         cudaFuncSetAttribute(pairs_mixed_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel<false, 4, MCMP2_GAUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PR_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel<true, 4, MCMP2_GAUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PR_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel<false, 4, MCMP2_BREIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PR_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(pairs_mixed_kernel<true, 4, MCMP2_BREIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PR_SMEM) != cudaSuccess) {
         err = "cannot reserve shared memory for the tensor-core kernels";
         return MCMP2_ECUDA;
     }
@@ -1324,7 +1607,7 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     int n_ptiles = 0;  // pair tiles: two p-blocks x one q-block, q-block >= the first p-block
     for (int b = 0; 2 * b < nb; ++b) n_ptiles += nb - 2 * b;
     PairArgs pa{a, partials, flag, s.m, n_tiles, n_ptiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda,
-                TIMEOUT_NS, 0};
+                TIMEOUT_NS, 0, r};
     if (plan.withhold_once_ns) {
         pa.withhold_first_copy = 1;
         pa.timeout_ns = plan.withhold_once_ns;
@@ -1349,6 +1632,12 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     if (plan.ncomp == 2)
         e = plan.tf32 ? cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<true, 2>, pmaps, pa)
                       : cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<false, 2>, pmaps, pa);
+    else if (s.interaction == MCMP2_GAUNT)
+        e = plan.tf32 ? cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<true, 4, MCMP2_GAUNT>, pmaps, pa)
+                      : cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<false, 4, MCMP2_GAUNT>, pmaps, pa);
+    else if (s.interaction == MCMP2_BREIT)
+        e = plan.tf32 ? cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<true, 4, MCMP2_BREIT>, pmaps, pa)
+                      : cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<false, 4, MCMP2_BREIT>, pmaps, pa);
     else
         e = plan.tf32 ? cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<true, 4>, pmaps, pa)
                       : cudaLaunchKernelEx(&cfg, pairs_mixed_kernel<false, 4>, pmaps, pa);

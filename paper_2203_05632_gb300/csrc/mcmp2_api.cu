@@ -909,8 +909,6 @@ int mcmp2_set_interaction(mcmp2_ctx *ctx, int interaction)
     if (!ctx) return MCMP2_EINVAL;
     if (interaction != MCMP2_COULOMB && interaction != MCMP2_GAUNT && interaction != MCMP2_BREIT)
         return ctx->fail(MCMP2_EINVAL, "unknown interaction");
-    if (interaction != MCMP2_COULOMB && ctx->precision != MCMP2_FP64)
-        return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt and Breit terms run in the FP64 form");
     if (interaction != MCMP2_COULOMB && ctx->loaded && ctx->sys.n_comp == 2)
         return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt / Breit terms need the small components");
     ctx->interaction = interaction;

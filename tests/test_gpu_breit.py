@@ -1,10 +1,21 @@
-"""The Gaunt and Breit interaction (Sec. II operator) in the FP64 form against the oracle.
+"""The Gaunt and Breit interaction (Sec. II operator) against the oracle.
 
-Parity bar as for the Coulomb FP64 form: 1e-10 relative per step estimate (relative to
-max(|I'_n|, 1e-3 <|f|>)).  Plus a walk on a system with order-one small components
-against the deterministic Coulomb + Gaunt MP2 energy (P4 with the Gaunt term), and the
-guards: the tensor-core forms and the adjoint keep the Coulomb operator, and checkpoints
-record the interaction.
+FP64 form: the parity bar of the Coulomb FP64 form, 1e-10 relative per step estimate
+(relative to max(|I'_n|, 1e-3 <|f|>)).  Tensor-core forms (split BF16 x3 and TF32, the
+operators applied to G- in the trace epilogue): the tolerance of the Coulomb operator in
+the same form, |got - want| <= REL |want| + ABS sum |f_pq| (REL = 2e-3, ABS = 1e-4 for
+split BF16 x3, whose products carry ~2^-16; both x 32 = 2^-11 / 2^-16 for TF32
+operands), with the absolute part scaled by sum_AB |c_A c_B| (6.25 Gaunt, 9 Breit):
+every operator combination is the Coulomb trace form of M_AB = O_A G- O_B, whose entries
+are entries of G- permuted and multiplied by unit phases (alpha_k), so each carries the
+Coulomb per-term error, weighted by |c_A c_B|.  (The worst-case bound from absolute
+expansions, 8 u |c_A c_B| times the traces of |O_A| |G-| |O_B| and |G+|, exceeds |I'_n|
+itself on these systems: the orbital sums cancel by three orders of magnitude.)  Plus a
+walk on a system with order-one small components against the deterministic Coulomb +
+Gaunt MP2 energy (P4 with the Gaunt term), split BF16 against the FP64 form on one walk
+(within a fifth of sigma-bar), and the guards: the adjoint keeps the Coulomb operator,
+two-component systems have no small components for it, and checkpoints record the
+interaction.
 """
 import numpy as np
 import pytest
@@ -24,6 +35,15 @@ def strong():
 
 def _ok(got, want, absmean):
     return np.abs(got - want) <= 1e-10 * np.maximum(np.abs(want), 1e-3 * absmean)
+
+
+REL_ABS = {pkg.MCMP2_MIXED: (2e-3, 1e-4), pkg.MCMP2_TF32: (6.4e-2, 3.2e-3)}
+C_SUM = {pkg.MCMP2_GAUNT: 6.25, pkg.MCMP2_BREIT: 9.0}
+
+
+def _tol(prec, interaction, want, abs_sum):
+    rel, ab = REL_ABS[prec]
+    return rel * np.abs(want) + ab * C_SUM[interaction] * abs_sum
 
 
 @pytest.mark.parametrize("interaction", [pkg.MCMP2_GAUNT, pkg.MCMP2_BREIT])
@@ -74,12 +94,94 @@ def test_gaunt_walk_matches_deterministic_gaunt_energy(strong):
     assert abs(res["energy"] - e_coul) > 5.0 * res["error"]
 
 
+@pytest.mark.parametrize("prec", [pkg.MCMP2_MIXED, pkg.MCMP2_TF32])
+@pytest.mark.parametrize("interaction", [pkg.MCMP2_GAUNT, pkg.MCMP2_BREIT])
+@pytest.mark.parametrize("m,n_tau", [(16, 1), (33, 2), (2, 1)])
+@pytest.mark.parametrize("which", ["tiny", "strong"])
+def test_interaction_tensor_forms_match_oracle(tiny, strong, prec, interaction, m, n_tau, which):
+    """Operator terms in the tensor-core trace epilogue: 1, 3 and 1 (ragged) 16-pair blocks."""
+    system = tiny if which == "tiny" else strong
+    orc = oracle.Oracle(system, interaction=interaction)
+    n = 2
+    r = synthetic.walker_positions(system.centres, n, m, seed=500 + m)
+    tau = synthetic.imaginary_times(orc.lam(), n, n_tau, seed=17 + m)
+    ctx = pkg.Context(system, m, n_tau, prec)
+    ctx.set_interaction(interaction)
+    got = ctx.eval_fixed(r, tau)
+    want, abs_sum = orc.eval_steps(r, tau, with_abs=True)
+    tol = _tol(prec, interaction, want, abs_sum)
+    assert np.all(np.abs(got - want) <= tol), (got, want, tol)
+    if which == "strong" and m > 2 and prec == pkg.MCMP2_MIXED:
+        # the operator terms move the estimate by far more than the split BF16 tolerance
+        ctx.set_interaction(pkg.MCMP2_COULOMB)
+        coul = ctx.eval_fixed(r, tau)
+        assert np.all(np.abs(coul - got) > 10.0 * tol), (coul, got, tol)
+
+
+@pytest.mark.parametrize("prec", [pkg.MCMP2_MIXED, pkg.MCMP2_TF32])
+def test_breit_tensor_forms_medium_system(prec):
+    medium = synthetic.make_system("medium")
+    orc = oracle.Oracle(medium, interaction=pkg.MCMP2_BREIT)
+    m, n_tau = 40, 2
+    r = synthetic.walker_positions(medium.centres, 1, m, seed=71)
+    tau = synthetic.imaginary_times(orc.lam(), 1, n_tau, seed=72)
+    ctx = pkg.Context(medium, m, n_tau, prec)
+    ctx.set_interaction(pkg.MCMP2_BREIT)
+    got = ctx.eval_fixed(r, tau)
+    want, abs_sum = orc.eval_steps(r, tau, with_abs=True)
+    assert np.all(np.abs(got - want) <= _tol(prec, pkg.MCMP2_BREIT, want, abs_sum)), (got, want)
+
+
+def test_breit_split_bf16_full_size_sampled_tiles():
+    """The bench launch (m = 1024 walker pairs, 4 times) with the Breit terms: sampled
+    16 x 16 tiles of the split BF16 x3 form against the oracle."""
+    medium = synthetic.make_system("medium")
+    orc = oracle.Oracle(medium, interaction=pkg.MCMP2_BREIT)
+    m, n_tau = 1024, 4
+    r = synthetic.walker_positions(medium.centres, 1, m, seed=81)
+    tau = synthetic.imaginary_times(orc.lam(), 1, n_tau, seed=82)
+    ctx = pkg.Context(medium, m, n_tau, pkg.MCMP2_MIXED)
+    ctx.set_interaction(pkg.MCMP2_BREIT)
+    step = ctx.eval_fixed(r, tau)[0]
+    partials, tp = ctx.debug_partials()
+    assert tp == 16
+    nb = (m + tp - 1) // tp
+    assert step == pytest.approx(partials.sum() / (m * (m - 1) / 2) / n_tau, rel=1e-12)
+    for bp, bq in [(0, 0), (9, 50), (nb - 1, nb - 1), (31, nb - 1)]:
+        pairs = [(bp * tp + i, bq * tp + j) for i in range(tp) for j in range(tp)
+                 if bp * tp + i < m and bq * tp + j < m and (bp < bq or i < j)]
+        ps, qs = np.array([p for p, _ in pairs]), np.array([q for _, q in pairs])
+        vals = orc.eval_pairs(r[0], tau[0], ps, qs)
+        want = vals.sum(axis=0)
+        k = sum(nb - b for b in range(bp)) + (bq - bp)
+        tol = _tol(pkg.MCMP2_MIXED, pkg.MCMP2_BREIT, want, np.abs(vals).sum(axis=0))
+        assert np.all(np.abs(partials[:, k] - want) <= tol), (bp, bq, partials[:, k], want, tol)
+
+
+def test_breit_split_bf16_agrees_with_fp64_form_within_a_fifth_of_sigma(strong):
+    """Same walk (FP64 sampling in both forms) with the Breit terms on the system with
+    order-one small components: the mean difference of the split BF16 and FP64 step
+    estimates is far below 0.2 sigma-bar of the FP64 run."""
+    m, n_tau, seed, n = 64, 2, 909, 400
+    r0 = synthetic.walker_positions(strong.centres, 1, m, seed=5)[0]
+    per = {}
+    for prec in (pkg.MCMP2_FP64, pkg.MCMP2_MIXED):
+        ctx = pkg.Context(strong, m, n_tau, prec)
+        ctx.set_interaction(pkg.MCMP2_BREIT)
+        ctx.set_walkers(r0, seed, 100)
+        per[prec] = np.array([ctx.run_steps(1, seed)["last_step"] for _ in range(n)])
+        ctx.close()
+    d = per[pkg.MCMP2_MIXED] - per[pkg.MCMP2_FP64]
+    I, s2, sb, nb = oracle.blocking(per[pkg.MCMP2_FP64])
+    assert nb == 4
+    assert abs(d.mean()) < 0.2 * sb, (d.mean(), sb)
+
+
 def test_guards_and_checkpoints(tiny):
-    for prec in (pkg.MCMP2_MIXED, pkg.MCMP2_TF32):
+    for prec in (pkg.MCMP2_MIXED, pkg.MCMP2_TF32):  # the tensor-core forms take every interaction
         ctx = pkg.Context(tiny, 16, 1, prec)
-        with pytest.raises(pkg.McMp2Error) as e:
-            ctx.set_interaction(pkg.MCMP2_GAUNT)
-        assert e.value.code == -7
+        ctx.set_interaction(pkg.MCMP2_GAUNT)
+        ctx.set_interaction(pkg.MCMP2_BREIT)
         ctx.set_interaction(pkg.MCMP2_COULOMB)
     ctx = pkg.Context(tiny, 16, 1, pkg.MCMP2_FP64)
     with pytest.raises(pkg.McMp2Error) as e:
