@@ -274,7 +274,7 @@ class Context:
         return {k: getattr(pc, k) for k, _ in pc._fields_} if mode == 0 else None
 
     def set_interaction(self, interaction: int):
-        """MCMP2_COULOMB (default), MCMP2_GAUNT or MCMP2_BREIT for the following steps (FP64 form)."""
+        """MCMP2_COULOMB (default), MCMP2_GAUNT or MCMP2_BREIT for the following steps (four-component systems)."""
         self._check(self.lib.mcmp2_set_interaction(self.h, int(interaction)))
 
     def test_stall_next(self, wait_limit_s: float):

@@ -37,7 +37,7 @@ struct DevSystem {
     double eps_homo, eps_lumo, lambda, Ng;
     const double *WL;          // FP64 large operand [n_l][2][n_orb][2] (L-alpha, L-beta; re, im)
     const double *WS;          // FP64 small operand [3 n_l][2][n_orb][2] (S-alpha, S-beta)
-    int interaction;           // MCMP2_COULOMB, MCMP2_GAUNT or MCMP2_BREIT (FP64 form only)
+    int interaction;           // MCMP2_COULOMB, MCMP2_GAUNT or MCMP2_BREIT (four-component systems)
     int n_comp;                // spinor components: 4, or 2 for two-component systems (FP64 form only)
 };
 

@@ -17,7 +17,8 @@
 //     in one accumulator, each real product as hi*hi + hi*lo + lo*hi (6 MMAs
 //     per 16-deep K step; 4 in TF32), then the direct and exchange traces of
 //     the trace form of Eq. MCMP2 for every pair of pairs, accumulated in FP64
-//     as Re f / (w w w).
+//     as Re f / (w w w); with the Gaunt / Breit terms of Sec. II the epilogue
+//     applies the operators to the G- rows (terms_part).
 // Every wait is bounded in time; on a time-out a kernel records it in a flag,
 // stops, drains its own copies, frees tensor memory and returns, and the host
 // reports MCMP2_ETIMEOUT.
