@@ -191,6 +191,8 @@ def main():
                     help="spinor components: 4, or 2 for the two-component variant")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form beside the mixed run")
     ap.add_argument("--tf32-steps", type=int, default=200, help="timed steps of the TF32 form beside the mixed run")
+    ap.add_argument("--breit-steps", type=int, default=100,
+                    help="timed steps of the same form with the full Breit interaction beside the Coulomb run")
     ap.add_argument("--stat-steps", type=int, default=10000, help="steps of the run that estimates sigma for time-to-0.1%%")
     ap.add_argument("--cpu-sample-m", type=int, default=1024)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
@@ -399,6 +401,23 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "peak_kind": "nominal FP64 CUDA-core rate"}
 
+    # The same form with the Breit terms of Sec. II in the trace epilogue (four-component
+    # spinors): the contraction's extra cost over the Coulomb operator.
+    breit = None
+    if prec != pkg.MCMP2_FP64 and inter == pkg.MCMP2_COULOMB and not two_c and args.breit_steps > 0:
+        bctx = pkg.Context(system, m_run, N_TAU, prec, device=local)
+        bctx.set_interaction(pkg.MCMP2_BREIT)
+        bctx.set_walkers(synthetic.walker_positions(system.centres, 1, m_run, seed=seed)[0], seed, 200)
+        bctx.run_steps(3, seed)
+        bctx.profile(1)
+        b_ms = time_steps(bctx, torch, args.breit_steps, seed, flush)
+        bp_ = bctx.profile(0)
+        bctx.profile(2)
+        breit = {"interaction": "breit (Coulomb + Gaunt + gauge)", "value": args.breit_steps * samples_per_step / (b_ms / 1e3),
+                 "ms_per_step": b_ms / args.breit_steps,
+                 "pair_kernel_ms": bp_["pair_ms"] / max(1, bp_["pair_launches"])}
+        bctx.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt, n, cores = cpu_oracle_rate(system, args.cpu_sample_m, N_TAU, steps=args.cpu_sample_steps,
@@ -432,6 +451,7 @@ def main():
             "time_to_0.1pct_soft_tiny": stat_soft,
             "fp64_form": fp64,
             "tf32_form": tf32,
+            "breit_form": breit,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
