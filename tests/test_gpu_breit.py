@@ -132,16 +132,18 @@ def test_breit_tensor_forms_medium_system(prec):
     assert np.all(np.abs(got - want) <= _tol(prec, pkg.MCMP2_BREIT, want, abs_sum)), (got, want)
 
 
-def test_breit_split_bf16_full_size_sampled_tiles():
-    """The bench launch (m = 1024 walker pairs, 4 times) with the Breit terms: sampled
-    16 x 16 tiles of the split BF16 x3 form against the oracle."""
+@pytest.mark.parametrize("prec,interaction", [(pkg.MCMP2_MIXED, pkg.MCMP2_BREIT), (pkg.MCMP2_MIXED, pkg.MCMP2_GAUNT),
+                                              (pkg.MCMP2_TF32, pkg.MCMP2_BREIT)])
+def test_interaction_full_size_sampled_tiles(prec, interaction):
+    """The bench launch (m = 1024 walker pairs, 4 times) with the operator terms: sampled
+    16 x 16 tiles of the tensor-core forms against the oracle."""
     medium = synthetic.make_system("medium")
-    orc = oracle.Oracle(medium, interaction=pkg.MCMP2_BREIT)
+    orc = oracle.Oracle(medium, interaction=interaction)
     m, n_tau = 1024, 4
     r = synthetic.walker_positions(medium.centres, 1, m, seed=81)
     tau = synthetic.imaginary_times(orc.lam(), 1, n_tau, seed=82)
-    ctx = pkg.Context(medium, m, n_tau, pkg.MCMP2_MIXED)
-    ctx.set_interaction(pkg.MCMP2_BREIT)
+    ctx = pkg.Context(medium, m, n_tau, prec)
+    ctx.set_interaction(interaction)
     step = ctx.eval_fixed(r, tau)[0]
     partials, tp = ctx.debug_partials()
     assert tp == 16
@@ -154,7 +156,7 @@ def test_breit_split_bf16_full_size_sampled_tiles():
         vals = orc.eval_pairs(r[0], tau[0], ps, qs)
         want = vals.sum(axis=0)
         k = sum(nb - b for b in range(bp)) + (bq - bp)
-        tol = _tol(pkg.MCMP2_MIXED, pkg.MCMP2_BREIT, want, np.abs(vals).sum(axis=0))
+        tol = _tol(prec, interaction, want, np.abs(vals).sum(axis=0))
         assert np.all(np.abs(partials[:, k] - want) <= tol), (bp, bq, partials[:, k], want, tol)
 
 
