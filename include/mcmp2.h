@@ -255,8 +255,9 @@ int mcmp2_restore(mcmp2_ctx *ctx, const void *buf_host, size_t bytes);
  * caller cannot create the workspace the other entry points need.
  *
  * It computes the same quantity as the contraction and reduction of the FP64
- * form: I'_n = (1/n_tau) sum_t (1/mC2) sum_{p<q} Re f/(w w w), and writes it
- * to out.  Inputs, all device pointers on the current device:
+ * form with the Coulomb interaction (there is no context, hence no
+ * mcmp2_set_interaction): I'_n = (1/n_tau) sum_t (1/mC2) sum_{p<q} Re f/(w w w),
+ * and writes it to out.  Inputs, all device pointers on the current device:
  *   phi   [8m][n_occ + n_vir] complex (re, im doubles): spinor value phi_k^c at
  *         row 4 x + c, position x = 2p + e (electron e of walker pair p),
  *         c = L-alpha, L-beta, S-alpha, S-beta; occupied columns first;
