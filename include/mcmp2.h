@@ -6,9 +6,10 @@
  * estimate of the second-order energy of Eq. FinalMP2 in the 13-dimensional
  * form of Eq. MCMP2 (Sec. III): a Metropolis move of m electron-pair walkers
  * under w(r1,r2) = g(r1) g(r2) / (N_g r12) (Eq. basisSet), large- and
- * kinetically balanced small-component basis values at the 2m positions
- * (Eq. C, Eq. KB), four-component spinors, imaginary times tau from the
- * inverse CDF of w(tau) = lambda exp(-lambda tau) (Eq. tauWeight), the 4x4
+ * kinetically balanced small-component basis values at the 2m positions (Eq. C
+ * with the kinetic-balance condition that follows it), four-component spinors,
+ * imaginary times tau from the inverse CDF of w(tau) = lambda exp(-lambda tau)
+ * (Eq. tauWeight), the 4x4
  * propagator blocks G-(x,y,-tau) and G+(x,y,tau) between all walker pairs,
  * and the traced direct and exchange products summed over all mC2 pairs of
  * pairs (Eq. redundant), with Flyvbjerg-Petersen blocking (Eq. uncertainty).
@@ -27,7 +28,7 @@
  *  - A context is not thread-safe; calls on one context must not overlap.
  *
  * Readings of the paper fixed by this interface:
- *  - Basis (Eq. C, Eq. KB, restricted kinetic balance): n_L real Cartesian
+ *  - Basis (Eq. C and the kinetic-balance condition after it, restricted kinetic balance): n_L real Cartesian
  *    Gaussians g_mu (shells of l = 0, 1, 2 expanded in the order s; x, y, z;
  *    xx, xy, xz, yy, yz, zz), g_mu(r) = coef (x-Ax)^a (y-Ay)^b (z-Az)^c
  *    exp(-alpha |r-A|^2).  Large 2-spinor basis {g_mu e_alpha, g_mu e_beta};
@@ -73,7 +74,13 @@ extern "C" {
 #define MCMP2_GAUNT 1  /* Coulomb + Gaunt */
 #define MCMP2_BREIT 2  /* Coulomb + Gaunt + gauge term */
 
-/* Sampling constants (Sec. III leaves them open; see the library design notes). */
+/* Sampling constants.  Sec. III (after Eq. basisSet) draws the walker pairs from
+ * w(r1,r2) by the Metropolis algorithm but leaves the proposal, its step size and
+ * the burn-in open.  Reading used here: a move displaces both electrons of a pair by
+ * independent uniform offsets in the cube [-delta, delta]^3 and is accepted with
+ * probability min(1, w'/w); delta starts at MCMP2_DELTA0 and, during burn-in only,
+ * is multiplied after every MCMP2_ADAPT_WINDOW steps by clamp(a / 0.5, 0.5, 2),
+ * a being the window's acceptance fraction; production steps keep delta fixed. */
 #define MCMP2_DELTA0 0.6        /* initial Metropolis displacement (bohr) */
 #define MCMP2_ADAPT_WINDOW 20   /* burn-in steps per displacement adaptation */
 #define MCMP2_BLOCK_SIZE 100    /* Flyvbjerg-Petersen block size N_b (Sec. IV) */
@@ -86,8 +93,8 @@ typedef struct {
     int n_functions;  /* n_L, scalar Cartesian Gaussians after shell expansion */
     int n_occ;        /* occupied positive-energy spinors (even, >= 2) */
     int n_vir;        /* virtual positive-energy spinors (even, >= 2) */
-    int m;            /* electron-pair walkers (>= 2) */
-    int n_tau;        /* imaginary times per step (>= 1) */
+    int m;            /* electron-pair walkers (2 <= m <= 65536) */
+    int n_tau;        /* imaginary times per step (1 <= n_tau <= 64) */
 } mcmp2_dims;
 
 /* Basis shells and the weight function g of Eq. basisSet. */
@@ -115,6 +122,7 @@ typedef struct {
 } mcmp2_result;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (plumbing of this library; the paper has no counterpart)
  * (a cudaStream_t; NULL for the legacy default stream) in `precision`
  * (MCMP2_FP64, MCMP2_MIXED or MCMP2_TF32).  Fails with MCMP2_EUNSUPPORTED on
  * devices other than compute capability 10.3. */
@@ -137,19 +145,27 @@ void mcmp2_destroy(mcmp2_ctx *ctx);
 /* Message of the last failed call on ctx (never NULL; "" if none). */
 const char *mcmp2_last_error(const mcmp2_ctx *ctx);
 
-/* Bytes of device workspace needed for `dims` in `precision`. */
+/* Bytes of device workspace needed for `dims` in `precision` (plumbing of this
+ * library; the paper has no counterpart). */
 int mcmp2_workspace_bytes(const mcmp2_dims *dims, int precision, size_t *bytes);
 
 /* Bind a device workspace (256-byte aligned, >= mcmp2_workspace_bytes) for `dims`.
- * Rebinding discards the loaded system, walkers and statistics. */
+ * The caller owns the memory and keeps it alive until mcmp2_destroy(); it is not
+ * freed by the library.  Rebinding discards the loaded system, walkers and
+ * statistics.  Plumbing of this library; the paper has no counterpart. */
 int mcmp2_bind_workspace(mcmp2_ctx *ctx, const mcmp2_dims *dims, void *dptr, size_t bytes);
 
-/* Load the system: basis shells and weight function, n_occ occupied then n_vir
- * virtual spinors with coefficients C_host (complex, [4 n_L][n_occ + n_vir]
- * row-major, rows L-alpha, L-beta, S-alpha, S-beta blocks) and energies
- * eps_host ([n_occ + n_vir]).  Sizes must match the bound dims.  Requires
- * max occupied eps < min virtual eps (lambda = 2 (eps_LUMO - eps_HOMO) > 0).
- * Host arrays are copied; N_g is evaluated in closed form. */
+/* Load the system: the inputs a Dirac-Hartree-Fock calculation furnishes
+ * (Sec. IV: MO coefficients and orbital energies) in the basis of Eq. C with
+ * kinetic balance, plus the weight-function parameters of Eq. basisSet
+ * (Table 1 layout).  n_occ occupied then n_vir virtual spinors with
+ * coefficients C_host (complex, [4 n_L][n_occ + n_vir] row-major, rows
+ * L-alpha, L-beta, S-alpha, S-beta blocks) and energies eps_host
+ * ([n_occ + n_vir]).  Sizes must match the bound dims (MCMP2_EINVAL).
+ * Requires max occupied eps < min virtual eps, so that the exponent of
+ * Eq. tauWeight, lambda = 2 (eps_LUMO - eps_HOMO), is positive (MCMP2_EINVAL);
+ * non-finite entries give MCMP2_ENONFINITE.  Host arrays are copied; N_g (the
+ * normalisation after Eq. basisSet) is evaluated in closed form. */
 int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n_vir,
                       const double *C_host, const double *eps_host);
 
@@ -169,38 +185,64 @@ int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n
 int mcmp2_load_system_2c(mcmp2_ctx *ctx, const mcmp2_basis *basis, int n_occ, int n_vir,
                          const double *C2_host, const double *eps_host);
 
-/* Set the m walker pairs from r_host ([m][2][3]), or, if r_host is NULL, draw
- * them from g(r1) g(r2) (each electron from the Gaussian mixture g; Philox
- * counters of the reserved step 2^64 - 1), and run `burn_in` Metropolis
- * steps with seed `seed` (steps numbered from 0), adapting the displacement
- * every MCMP2_ADAPT_WINDOW steps by delta <- delta * clamp(a/0.5, 0.5, 2) with
- * a the window's acceptance fraction.  Resets the statistics and the step
- * counter to burn_in. */
+/* Walker pairs for the Metropolis walk of Sec. III (after Eq. basisSet: the
+ * pairs are distributed as w(r1, r2) by the Metropolis algorithm; the burn-in
+ * steps are excluded from the statistics of Eq. uncertainty).  Sets the m walker
+ * pairs from r_host ([m][2][3], bohr), or, if r_host is NULL, draws them from
+ * g(r1) g(r2) (each electron from the Gaussian mixture g; Philox counters of the
+ * reserved step 2^64 - 1), and runs `burn_in` Metropolis steps with seed `seed`
+ * (steps numbered from 0), adapting the displacement every MCMP2_ADAPT_WINDOW
+ * steps by delta <- delta * clamp(a/0.5, 0.5, 2) with a the window's acceptance
+ * fraction.  Resets the statistics and the step counter to burn_in.
+ * MCMP2_ENONFINITE for a non-finite position, MCMP2_ENOTLOADED before a system. */
 int mcmp2_set_walkers(mcmp2_ctx *ctx, const double *r_host, uint64_t seed, int64_t burn_in);
 
-/* Run n production steps with seed `seed`: Metropolis move, n_tau inverse-CDF
- * times, the pair-of-pairs estimate I'_n and the blocking update, all on the
- * device.  Steps continue the context's step counter, so consecutive calls
- * with one seed equal one call.  Writes the running statistics to out_host
- * (may be NULL; then nothing is copied back). */
+/* Run n production steps with seed `seed`, all on the device: the Metropolis
+ * move (Sec. III), n_tau imaginary times by the inverse CDF of Eq. tauWeight,
+ * the redundant-walker estimate I'_n of Eq. redundant over all mC2 pairs of
+ * walker pairs, and the blocking update of Eq. uncertainty (N_b =
+ * MCMP2_BLOCK_SIZE).  Steps continue the context's step counter, so consecutive
+ * calls with one seed equal one call.  Writes the running statistics to
+ * out_host (may be NULL; then nothing is copied back and the call does not wait
+ * for the device).  MCMP2_ENOTLOADED without walkers; MCMP2_ENONFINITE if a step
+ * estimate is not finite; MCMP2_ETIMEOUT if a bounded device wait ran out. */
 int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out_host);
 
-/* Replay mode: evaluate I'_n for n given samples without moving walkers or
- * touching the statistics.  r_host: [n][m][2][3]; tau_host: [n][n_tau] (> 0);
- * per_step_host: [n] output. */
+/* Replay mode: evaluate I'_n of Eq. redundant for n given samples (positions
+ * and imaginary times supplied by the caller instead of drawn), without moving
+ * walkers or touching the statistics.  r_host: [n][m][2][3]; tau_host:
+ * [n][n_tau] (finite, >= 0, else MCMP2_EINVAL); per_step_host: [n] output. */
 int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double *tau_host,
                      double *per_step_host);
 
-/* Copy the current walker positions ([m][2][3]) and displacement to the host. */
+/* Copy the current walker positions ([m][2][3]) and the Metropolis displacement
+ * delta to the host (either pointer may be NULL). */
 int mcmp2_get_walkers(mcmp2_ctx *ctx, double *r_host, double *delta_host);
 
 /* Per-tile partial sums of the latest step, for sampled checks at full size:
- * out_host[t * n_tiles + k] = sum over the pairs (p < q) of tile k of
- * Re f/(w w w) at time t, tiles of `tile_pairs` pairs per side enumerated
- * row by row over the upper triangle (bp <= bq).  *n_tiles and *tile_pairs
- * are written; capacity is the length of out_host in doubles. */
+ * out_host[t * n_tiles + k] = sum over the pairs (p < q) of tile k of the
+ * summand Re f/(w w w) of Eq. redundant at time t, tiles of `tile_pairs` pairs
+ * per side enumerated row by row over the upper triangle (bp <= bq).
+ * *n_tiles and *tile_pairs are written; capacity is the length of out_host in
+ * doubles (MCMP2_ENOSPACE if short; out_host NULL only reports the sizes). */
 int mcmp2_debug_partials(mcmp2_ctx *ctx, double *out_host, size_t capacity, int *n_tiles,
                          int *tile_pairs);
+
+/* Element-by-element record of one tile of the pair-of-pairs sum of Eq. redundant,
+ * for checking every summand at full size.  Evaluates one replay step for the
+ * positions r_host ([m][2][3]) and times tau_host ([n_tau], finite, >= 0) with the
+ * kernels and launch shape of mcmp2_eval_fixed, and records for the tile (bp, bq)
+ * of T x T walker pairs (T = tile_pairs: 8 in the FP64 form, 16 in the
+ * tensor-core forms, 32 for two-component systems there; 0 <= bp <= bq <
+ * ceil(m / T), else MCMP2_EINVAL) every summand
+ *   out_host[(t T + i) T + j] = Re f(p, q, tau_t) / (w(r1p, r2p) w(r1q, r2q) w(tau_t)),
+ *   p = bp T + i, q = bq T + j,
+ * with the loaded interaction, for p < q < m, and 0 for the other entries.
+ * capacity >= n_tau T^2 doubles (MCMP2_ENOSPACE).  *step_host (may be NULL)
+ * receives that step's I'_n, *tile_pairs (may be NULL) receives T.  The walk
+ * and the statistics are untouched. */
+int mcmp2_debug_elements(mcmp2_ctx *ctx, const double *r_host, const double *tau_host, int bp, int bq,
+                         double *out_host, size_t capacity, double *step_host, int *tile_pairs);
 
 /* Gradient of the replay estimate E = (1/n) sum_n I'_n for the n given samples
  * (common random numbers: r_host [n][m][2][3], tau_host [n][n_tau] as in
@@ -216,7 +258,8 @@ int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double
                    double *d_eps_host, double *d_C_host);
 
 /* Launch counters and CUDA-event timing of the pair-of-pairs contraction
- * kernel (the dominant kernel), measured on the context's stream. */
+ * kernel (the dominant kernel), measured on the context's stream.  Measurement
+ * plumbing of this library; the paper has no counterpart. */
 typedef struct {
     int64_t launches;       /* kernels this context launched since the last reset */
     int64_t pair_launches;  /* launches of the pair-of-pairs contraction kernel */
@@ -237,10 +280,14 @@ int mcmp2_profile(mcmp2_ctx *ctx, int mode, mcmp2_profile_counters *out_host);
  * reporting without a device fault. */
 int mcmp2_test_stall_next(mcmp2_ctx *ctx, double wait_limit_s);
 
-/* Size of a checkpoint (walkers, displacement, step counter, statistics,
- * system digest) and its serialisation into / restoration from a host
- * buffer.  Restoring into a context with the same system and dims continues
- * bit-identically. */
+/* Restartable runs (Sec. III, last paragraph: each processor records its
+ * number of steps, I_N and sigma-bar_N, so a run can be resumed, and resumed
+ * indefinitely).  Size of a checkpoint (walkers, displacement, step counter,
+ * statistics, digest of the system and interaction) and its serialisation into /
+ * restoration from a host buffer.  Restoring into a context with the same system,
+ * interaction and dims continues bit-identically; anything else gives
+ * MCMP2_EINVAL, a short buffer MCMP2_ENOSPACE (checkpoint) or MCMP2_EINVAL
+ * (restore). */
 int mcmp2_checkpoint_bytes(const mcmp2_ctx *ctx, size_t *bytes);
 int mcmp2_checkpoint(mcmp2_ctx *ctx, void *buf_host, size_t capacity);
 int mcmp2_restore(mcmp2_ctx *ctx, const void *buf_host, size_t bytes);
@@ -275,15 +322,18 @@ int mcmp2_restore(mcmp2_ctx *ctx, const void *buf_host, size_t bytes);
  * loads the library until the process exits.  It needs
  * n_tau * ceil(m/8) (ceil(m/8) + 1) / 2 <= MCMP2_NOALLOC_MAX_PARTIALS (for
  * example m = 1024 with n_tau <= 7); larger sizes return MCMP2_ENOSPACE
- * before any work is issued.  The array is shared by all calls and keeps the
+ * before any work is issued; m <= 65536 and n_tau <= 64 as for a context
+ * (MCMP2_EINVAL otherwise).  The array is shared by all calls and keeps the
  * last call's contents; every entry a call reads is first written by that
  * call, and the reduction's completion counter is cleared at the start of
  * each call.  Calls that overlap on the GPU (on
  * different streams, or from different threads) race on the array and give
  * wrong results: serialise them.  The first call on each device looks up the
  * array's device address (with that device current); make that first call
- * before any stream capture.  No cudaMalloc, cudaFree or other allocating
- * routine is called.
+ * before any stream capture.  The address is kept for the life of the
+ * process, so resetting a device (cudaDeviceReset) after the first call on it
+ * is not supported.  No cudaMalloc, cudaFree or other allocating routine is
+ * called.
  * Returns MCMP2_OK, MCMP2_EINVAL (bad sizes, null pointers, lambda), MCMP2_ENOSPACE
  * (sizes beyond the scratch array) or MCMP2_ECUDA (a launch failed). */
 #define MCMP2_NOALLOC_MAX_PARTIALS 65536

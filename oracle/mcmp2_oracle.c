@@ -10,7 +10,7 @@
  * readings listed where the text is silent or garbled.
  *
  * Readings of the paper used here:
- *  - Eq. C with kinetic balance (Eq. KB): n_L real Cartesian Gaussians g_mu.
+ *  - Eq. C with its kinetic-balance condition: n_L real Cartesian Gaussians g_mu.
  *    The large 2-spinor basis is {g_mu e_alpha, g_mu e_beta}; the small one
  *    is {i(sigma.p)(g_mu e_s)} = {(sigma.grad)(g_mu e_s)} (restricted kinetic
  *    balance, p = -i grad).  C has 4 n_L rows: L-alpha, L-beta, S-alpha,
@@ -60,7 +60,7 @@ typedef struct {
 } or_system;
 
 /* ---------------------------------------------------------------------- */
-/* Basis functions (Eq. C, Eq. KB)                                         */
+/* Basis functions (Eq. C and its kinetic-balance condition)               */
 /* ---------------------------------------------------------------------- */
 
 static const int CART[3][6][3] = {
@@ -113,7 +113,7 @@ void or_basis_at(const or_system *s, const double *r, double *val, double *grad)
 
 /* Four-component spinor values phi_k^c(r), c = L-alpha, L-beta, S-alpha, S-beta.
  * Large components by Eq. C; small components by applying sigma.grad to the
- * 2-spinor g_mu e_s (Eq. KB with i(sigma.p) = sigma.grad).
+ * 2-spinor g_mu e_s (kinetic balance with i(sigma.p) = sigma.grad).
  * phi: complex interleaved [n_orb][4]. */
 void or_spinors_at(const or_system *s, const double *r, double *phi_out)
 {

@@ -20,7 +20,7 @@ def real_function_coefficients(system) -> np.ndarray:
     """U[c, P, k] with phi_k^c(r) = sum_P U[c, P, k] f_P(r).
 
     Large components follow Eq. C directly; the small 2-spinor is
-    sum_mu sum_s C^{S s}_{mu k} (sigma.grad)(g_mu e_s) (Eq. KB), i.e.
+    sum_mu sum_s C^{S s}_{mu k} (sigma.grad)(g_mu e_s) (kinetic balance, after Eq. C), i.e.
     component c' of it takes sigma_j[c', s] C^{S s}_{mu k} on f_{4mu+1+j}."""
     n_l = system.n_l
     n = system.n_orb

@@ -6,7 +6,7 @@
  * estimate on small systems.  The spinor integrals (ia|jb) of the paper's
  * two-electron integral definition are expanded over the real functions
  *   f_{4 mu + 0} = g_mu,  f_{4 mu + j} = d g_mu / d x_j  (j = 1, 2, 3),
- * which span the large (Eq. C) and kinetically balanced small (Eq. KB)
+ * which span the large (Eq. C) and kinetically balanced small (the kinetic-balance condition after Eq. C)
  * components.  This file computes (PQ|RS) over those real functions with the
  * McMurchie-Davidson scheme (Hermite expansion of Gaussian products and the
  * Boys function), written from the mathematics; the spinor transformation and

@@ -79,6 +79,8 @@ SIGNATURES = {
     "mcmp2_get_walkers": (_I, [_P, _P, _P]),
     "mcmp2_backward": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
     "mcmp2_debug_partials": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mcmp2_debug_elements": (_I, [_P, _P, _P, _I, _I, _P, _SZ, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(_I)]),
     "mcmp2_profile": (_I, [_P, _I, ctypes.POINTER(ProfileCounters)]),
     "mcmp2_test_stall_next": (_I, [_P, ctypes.c_double]),
     "mcmp2_set_interaction": (_I, [_P, _I]),
@@ -266,6 +268,27 @@ class Context:
         self._check(self.lib.mcmp2_debug_partials(self.h, _ptr(out), out.size, ctypes.byref(nt),
                                                   ctypes.byref(tp)))
         return out, tp.value
+
+    def tile_pairs(self) -> int:
+        """Walker pairs per side of the contraction's tiles (8 FP64, 16 tensor-core, 32 two-component there)."""
+        nt, tp = _I(0), _I(0)
+        self._check(self.lib.mcmp2_debug_partials(self.h, None, 0, ctypes.byref(nt), ctypes.byref(tp)))
+        return tp.value
+
+    def debug_elements(self, r_step, tau_step, bp: int, bq: int):
+        """Every summand Re f/(w w w) of the tile (bp, bq) for one replay step:
+        returns (elements [n_tau][T][T], I'_n of the step, T)."""
+        r = _c(r_step, np.float64)
+        tau = _c(tau_step, np.float64)
+        assert r.shape == (self.m, 2, 3) and tau.shape == (self.n_tau,)
+        tp = self.tile_pairs()
+        out = np.zeros((self.n_tau, tp, tp))
+        step = ctypes.c_double(0.0)
+        got = _I(0)
+        self._check(self.lib.mcmp2_debug_elements(self.h, _ptr(r), _ptr(tau), int(bp), int(bq), _ptr(out), out.size,
+                                                  ctypes.byref(step), ctypes.byref(got)))
+        assert got.value == tp
+        return out, step.value, tp
 
     def profile(self, mode: int = 0):
         """mode 1: reset and time the contraction kernel; 2: reset, no timing; 0: read."""

@@ -47,6 +47,7 @@ def up_to_date() -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
+        build_probes()
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -73,7 +74,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_probes(force=force)
     return LIB
+
+
+PROBES = os.path.join(HERE, "probes")
+PROBE_LIB = os.path.join(BUILD, "libprobes.so")
+
+
+def build_probes(force: bool = False) -> str:
+    """Measurement probes (not part of the C ABI): _build/libprobes.so."""
+    srcs = sorted(os.path.join(PROBES, f) for f in os.listdir(PROBES) if f.endswith(".cu"))
+    if not force and os.path.exists(PROBE_LIB) and all(os.path.getmtime(s) <= os.path.getmtime(PROBE_LIB)
+                                                        for s in srcs):
+        return PROBE_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PROBE_LIB + f".{os.getpid()}.tmp"
+    r = subprocess.run([nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, *srcs,
+                        "-cudart", "static"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on the probes:\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

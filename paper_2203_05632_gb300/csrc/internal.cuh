@@ -97,6 +97,15 @@ __device__ __forceinline__ double weight_g(const DevSystem &s, double x, double 
     return g;
 }
 
+// Optional record of the per-element values of one tile of the pair-of-pairs sum
+// (mcmp2_debug_elements): for the tile (bp, bq) of tp x tp walker pairs,
+// out[(t tp + i) tp + j] = Re f/(w w w) of p = bp tp + i, q = bq tp + j at time t
+// (0 where p >= q or either index is past m).  out == nullptr: nothing recorded.
+struct DebugTile {
+    double *out = nullptr;
+    int bp = -1, bq = -1;
+};
+
 // Records ev on st; while st is being captured into a graph the record becomes
 // an external event node, so the event can be read after each replay.
 inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t st)
@@ -128,7 +137,8 @@ cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi,
 cudaError_t prepare_f64();  // sets the FP64 contraction kernel's shared-memory limit
 // r (positions [m][2][3]) is read for the Breit gauge term only; it may be null otherwise.
 cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale,
-                             const double *a, double *partials, cudaStream_t st, const double *r = nullptr);
+                             const double *a, double *partials, cudaStream_t st, const double *r = nullptr,
+                             const DebugTile &dbg = DebugTile{});
 
 size_t adjoint_smem_bytes();
 cudaError_t launch_adjoint_time(const DevSystem &s, const double *B, const double *phi, const double *scale,
@@ -147,10 +157,16 @@ cudaError_t launch_reduce(const DevSystem &s, const double *partials, int n_tile
                           ReduceScratch *scratch, cudaStream_t st, const int *abort_flag = nullptr);
 
 __host__ __device__ inline int pair_blocks(int m, int tile_pairs) { return (m + tile_pairs - 1) / tile_pairs; }
-__host__ __device__ inline int n_tiles_for(int m, int tile_pairs)
+// Tiles of the upper triangle, counted in 64 bits: for the largest m the API
+// accepts (MAX_WALKER_PAIRS) the count stays far below 2^31.
+__host__ __device__ inline long long n_tiles_for(int m, int tile_pairs)
 {
-    const int nb = pair_blocks(m, tile_pairs);
+    const long long nb = pair_blocks(m, tile_pairs);
     return nb * (nb + 1) / 2;
 }
+// Largest number of walker pairs any entry point accepts: 8,390,656 FP64 tiles
+// of 8 pairs, so every tile count and grid dimension fits an int.
+constexpr int MAX_WALKER_PAIRS = 1 << 16;
+constexpr int MAX_TAU = 64;  // imaginary times per step
 
 }  // namespace mcmp2

@@ -351,15 +351,14 @@ cudaError_t launch_adjoint_time(const DevSystem &s, const double *B, const doubl
                                 double *Ys, double *partials, double *GWL, double *GWS, double *d_eps,
                                 cudaStream_t st)
 {
-    static bool configured = false;
+    // The shared-memory opt-in belongs to the current device's context: set on every call (cheap).
     const size_t smem = sizeof(AdjSmem);
-    if (!configured) {
+    {
         const cudaError_t e =
             cudaFuncSetAttribute(adjoint_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
-    const int n_tiles = n_tiles_for(s.m, TP);
+    const int n_tiles = (int)n_tiles_for(s.m, TP);
     adjoint_tiles_kernel<<<n_tiles, 256, smem, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, a, t_index,
                                                      norm, reinterpret_cast<double2 *>(Ybar), partials, n_tiles);
     adjoint_eps_kernel<<<s.n_orb, 256, 0, st>>>(s, reinterpret_cast<const double2 *>(phi), scale, tau, t_index,

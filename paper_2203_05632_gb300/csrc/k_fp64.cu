@@ -110,7 +110,7 @@ static cudaError_t gemm_rm(int M, int N, int K, const T *A, int lda, const T *B,
 
 // Spinor values phi[x][c][k] (complex, c = L-alpha, L-beta, S-alpha, S-beta):
 // the large components contract basis values with C^L (Eq. C); the small ones
-// contract the gradients with the Pauli-folded C^S (Eq. KB).  Two-component
+// contract the gradients with the Pauli-folded C^S (the kinetic-balance condition after Eq. C).  Two-component
 // systems (s.n_comp == 2) have the large components only: phi[x][c][k], c =
 // alpha, beta.
 cudaError_t launch_spinors_f64(const DevSystem &s, const double *B, double *phi, cudaStream_t st)
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
                                                            const double *__restrict__ scale,
                                                            const double *__restrict__ a,
                                                            double *__restrict__ partials, int n_tiles,
-                                                           const double *__restrict__ r)
+                                                           const double *__restrict__ r, DebugTile dbg)
 {
     static_assert(NC == 4 || (NC == 2 && !WITH_TERMS), "Gaunt / Breit terms need the small components");
     constexpr int NN = NC * NC, ROWS = 16 * NC;
@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
             if constexpr (WITH_TERMS) F = breit_value(s.interaction, M1, M3, N11, N22, M2, M4, r, p, q);
             v = F * a[p] * a[q] / s.lambda;
         }
+        if (dbg.out && bp == dbg.bp && bq == dbg.bq) dbg.out[((size_t)t * F64_TP + px) * F64_TP + qy] = v;
         sm.part[tid] = v;
     }
     __syncthreads();
@@ -443,10 +444,20 @@ __global__ void __launch_bounds__(256, 1) pairs_f64_kernel(DevSystem s, const do
     }
 }
 
-static bool g_f64_configured = false;
+// The shared-memory opt-in is a property of each device's context: remembered per device.
+constexpr int F64_MAX_DEVICES = 64;
+static bool g_f64_configured[F64_MAX_DEVICES] = {};
+
+static int current_device()
+{
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < F64_MAX_DEVICES ? dev : -1;
+}
 
 cudaError_t prepare_f64()
 {
+    const int dev = current_device();
+    if (dev < 0) return cudaErrorInvalidDevice;
     cudaError_t e = cudaFuncSetAttribute(pairs_f64_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(F64Smem<4>));
     if (e == cudaSuccess)
@@ -455,28 +466,29 @@ cudaError_t prepare_f64()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pairs_f64_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(F64Smem<2>));
-    if (e == cudaSuccess) g_f64_configured = true;
+    if (e == cudaSuccess) g_f64_configured[dev] = true;
     return e;
 }
 
 cudaError_t launch_pairs_f64(const DevSystem &s, const double *phi, const double *scale, const double *a,
-                             double *partials, cudaStream_t st, const double *r)
+                             double *partials, cudaStream_t st, const double *r, const DebugTile &dbg)
 {
     if (s.interaction >= 2 && !r) return cudaErrorInvalidValue;
     if (s.n_comp == 2 && s.interaction > 0) return cudaErrorInvalidValue;
-    if (!g_f64_configured) {
+    const int dev = current_device();
+    if (dev < 0 || !g_f64_configured[dev]) {
         const cudaError_t e = prepare_f64();
         if (e != cudaSuccess) return e;
     }
-    const int n_tiles = n_tiles_for(s.m, F64_TP);
+    const int n_tiles = (int)n_tiles_for(s.m, F64_TP);
     dim3 grid(n_tiles, s.n_tau);
     const double2 *ph = reinterpret_cast<const double2 *>(phi);
     if (s.n_comp == 2)
-        pairs_f64_kernel<false, 2><<<grid, 256, sizeof(F64Smem<2>), st>>>(s, ph, scale, a, partials, n_tiles, r);
+        pairs_f64_kernel<false, 2><<<grid, 256, sizeof(F64Smem<2>), st>>>(s, ph, scale, a, partials, n_tiles, r, dbg);
     else if (s.interaction > 0)
-        pairs_f64_kernel<true, 4><<<grid, 256, sizeof(F64Smem<4>), st>>>(s, ph, scale, a, partials, n_tiles, r);
+        pairs_f64_kernel<true, 4><<<grid, 256, sizeof(F64Smem<4>), st>>>(s, ph, scale, a, partials, n_tiles, r, dbg);
     else
-        pairs_f64_kernel<false, 4><<<grid, 256, sizeof(F64Smem<4>), st>>>(s, ph, scale, a, partials, n_tiles, r);
+        pairs_f64_kernel<false, 4><<<grid, 256, sizeof(F64Smem<4>), st>>>(s, ph, scale, a, partials, n_tiles, r, dbg);
     return cudaGetLastError();
 }
 

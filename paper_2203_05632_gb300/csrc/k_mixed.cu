@@ -467,6 +467,7 @@ struct PairArgs {
     unsigned long long timeout_ns;  // limit of every wait
     int withhold_first_copy;        // test hook: never issue the first stage's copy (its wait runs out)
     const double *r = nullptr;      // walker positions [m][2][3] (the Breit terms' unit vectors)
+    DebugTile dbg{};                // optional per-element record of one TP x TP tile
 };
 
 // Pair tile k -> (BP, bq): row BP of the enumeration holds bq = 2 BP .. nb - 1.
@@ -891,6 +892,9 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
                 part += __shfl_xor_sync(0xffffffffu, part, 4);
                 const bool valid = p < args.m && q < args.m && (bp < bq || (bp == bq && p_local < ql));
                 if (valid) acc += (double)(-0.5f * part) * a_q;
+                if (args.dbg.out && bp == args.dbg.bp && bq == args.dbg.bq && (lane & 7) == 0)
+                    args.dbg.out[((size_t)t * 16 + p_local) * 16 + ql] =
+                        valid ? (double)(-0.5f * part) * a_q * args.a[p] * args.inv_lambda : 0.0;
             }
         }
 #pragma unroll 1
@@ -968,6 +972,9 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
                 const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
                 const bool valid = p < args.m && q < args.m && (bp < bq || (bp == bq && p_local < ql));
                 if (valid) acc += (double)(-0.5f * (direct_re - xr)) * a_q;
+                if (args.dbg.out && bp == args.dbg.bp && bq == args.dbg.bq && (lane & 7) == 0)
+                    args.dbg.out[((size_t)t * 16 + p_local) * 16 + ql] =
+                        valid ? (double)(-0.5f * (direct_re - xr)) * a_q * args.a[p] * args.inv_lambda : 0.0;
             }
         }
         fence_before();
@@ -1102,6 +1109,9 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
                 const double a_q = __shfl_sync(0xffffffffu, a_lane, ql);
                 const bool valid = p < args.m && q < args.m && (bp < bq || (bp == bq && p_local < ql));
                 if (valid) acc += (double)(-0.5f * (direct_re - xr)) * a_q;
+                if (args.dbg.out && bp == args.dbg.bp && bq == args.dbg.bq && (lane & 3) == 0)
+                    args.dbg.out[((size_t)t * 32 + p_local) * 32 + ql] =
+                        valid ? (double)(-0.5f * (direct_re - xr)) * a_q * args.a[p] * args.inv_lambda : 0.0;
             }
         }
         fence_before();
@@ -1573,7 +1583,7 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
 
 int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *r,
                const float *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
-               cudaEvent_t *ev, int *n_launches, int *n_pair_launches)
+               cudaEvent_t *ev, int *n_launches, int *n_pair_launches, const DebugTile &dbg)
 {
     if (!plan.ready) {
         err = "mixed path not prepared";
@@ -1609,6 +1619,7 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     for (int b = 0; 2 * b < nb; ++b) n_ptiles += nb - 2 * b;
     PairArgs pa{a, partials, flag, s.m, n_tiles, n_ptiles, nb, s.n_tau, s.n_occ, s.n_vir, 1.0 / s.lambda,
                 TIMEOUT_NS, 0, r};
+    pa.dbg = dbg;
     if (plan.withhold_once_ns) {
         pa.withhold_first_copy = 1;
         pa.timeout_ns = plan.withhold_once_ns;

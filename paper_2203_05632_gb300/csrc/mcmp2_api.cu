@@ -25,6 +25,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t centres, wcoef, shell_centre, shell_alpha, shell_coef, fn_shell, fn_pow, eps, WL, WS;
     size_t r, a, tau, scale, scale_f, step, burn_acc, stats, per_step, stage_r, stage_tau, red, cdf;
+    size_t elements;  // per-element record of one tile: [n_tau][32][32] doubles (the largest tile)
     size_t B, phi, partials;
     size_t Ybar, Ys, GWL, GWS, d_eps;  // adjoint buffers (FP64 form)
     MixedLayout mixed;
@@ -36,7 +37,7 @@ bool dims_valid(const mcmp2_dims *d)
 {
     return d && d->n_centres >= 1 && d->n_functions >= 1 && d->n_occ >= 2 && d->n_vir >= 2 && d->m >= 2 &&
            d->n_tau >= 1 && d->n_occ % 2 == 0 && d->n_vir % 2 == 0 && d->n_functions <= 65536 &&
-           d->m <= (1 << 20) && d->n_tau <= 64 && d->n_occ + d->n_vir <= 65536;
+           d->m <= MAX_WALKER_PAIRS && d->n_tau <= MAX_TAU && d->n_occ + d->n_vir <= 65536;
 }
 
 Layout make_layout(const mcmp2_dims &d, int precision)
@@ -72,6 +73,7 @@ Layout make_layout(const mcmp2_dims &d, int precision)
     L.per_step = take(REPLAY_CHUNK * 8);
     L.stage_r = take(REPLAY_CHUNK * m * 6 * 8);
     L.stage_tau = take(REPLAY_CHUNK * d.n_tau * 8);
+    L.elements = take((size_t)d.n_tau * TILE_PAIRS_MIXED_2C * TILE_PAIRS_MIXED_2C * 8);
     if (precision == MCMP2_FP64) {
         L.tile_pairs = TILE_PAIRS_F64;
         L.B = take(2 * m * 4 * nl * 8);
@@ -86,7 +88,7 @@ Layout make_layout(const mcmp2_dims &d, int precision)
         L.mixed = mixed_layout(d.m, d.n_functions, d.n_occ, d.n_vir, d.n_tau, off);
         off = align256(L.mixed.end);
     }
-    L.n_tiles = n_tiles_for(d.m, L.tile_pairs);
+    L.n_tiles = (int)n_tiles_for(d.m, L.tile_pairs);
     L.partials = take((size_t)d.n_tau * L.n_tiles * 8);
     L.total = off;
     return L;
@@ -423,7 +425,7 @@ int load_system_impl(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir,
     S.n_comp = n_comp;
     if (ctx->precision != MCMP2_FP64) {  // a two-component tile holds 32 pairs (4 operand rows each)
         ctx->L.tile_pairs = n_comp == 2 ? TILE_PAIRS_MIXED_2C : TILE_PAIRS_MIXED;
-        ctx->L.n_tiles = n_tiles_for(d.m, ctx->L.tile_pairs);
+        ctx->L.n_tiles = (int)n_tiles_for(d.m, ctx->L.tile_pairs);
     }
 
     uint64_t h = 1469598103934665603ull;
@@ -509,7 +511,7 @@ int reset_stats(mcmp2_ctx *ctx)
 // given) to I'_n in out_slot.  Optionally updates statistics and advances the step.
 int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uint64_t seed, double *out_slot,
                    int update, bool advance, bool weights_ready = false, cudaStream_t st_in = nullptr,
-                   cudaEvent_t *fixed_ev = nullptr)
+                   cudaEvent_t *fixed_ev = nullptr, const DebugTile &dbg = DebugTile{})
 {
     const Layout &L = ctx->L;
     const DevSystem &S = ctx->sys;
@@ -542,14 +544,14 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         CK(launch_basis<double>(S, r, B, st), "basis values");
         CK(launch_spinors_f64(S, B, phi, st), "spinor formation");
         if (e0) CK(record_event(e0, st), "event");
-        CK(launch_pairs_f64(S, phi, scale, a, partials, st, r), "pair-of-pairs tiles");
+        CK(launch_pairs_f64(S, phi, scale, a, partials, st, r, dbg), "pair-of-pairs tiles");
         if (e1) CK(record_event(e1, st), "event");
         ctx->launches += 4;
         ctx->pair_launches += 1;
     } else {
         int n_launch = 0, n_pair = 0;
         const int rc = mixed_step(ctx->mixed, S, L.mixed, ctx->ws, r, scale_f, a, partials, st, ctx->err,
-                                  ev[0] ? ev : nullptr, &n_launch, &n_pair);
+                                  ev[0] ? ev : nullptr, &n_launch, &n_pair, dbg);
         if (rc != MCMP2_OK) return rc;
         ctx->launches += n_launch;
         ctx->pair_launches += n_pair;
@@ -873,6 +875,48 @@ int mcmp2_debug_partials(mcmp2_ctx *ctx, double *out, size_t capacity, int *n_ti
     CK(cudaMemcpyAsync(out, ctx->ws + ctx->L.partials, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
        "copy partials");
     CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return MCMP2_OK;
+}
+
+int mcmp2_debug_elements(mcmp2_ctx *ctx, const double *r_host, const double *tau_host, int bp, int bq,
+                         double *out_host, size_t capacity, double *step_host, int *tile_pairs)
+{
+    if (!ctx) return MCMP2_EINVAL;
+    if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
+    const int m = ctx->dims.m, nt = ctx->dims.n_tau, tp = ctx->L.tile_pairs;
+    if (tile_pairs) *tile_pairs = tp;
+    if (!r_host || !tau_host || !out_host) return ctx->fail(MCMP2_EINVAL, "bad element-record arguments");
+    const int nb = pair_blocks(m, tp);
+    if (bp < 0 || bq < bp || bq >= nb) return ctx->fail(MCMP2_EINVAL, "tile (%d, %d) outside 0 <= bp <= bq < %d", bp, bq, nb);
+    const size_t need = (size_t)nt * tp * tp;
+    if (capacity < need) return ctx->fail(MCMP2_ENOSPACE, "need %zu doubles", need);
+    if (!all_finite(r_host, (size_t)m * 6)) return ctx->fail(MCMP2_ENONFINITE, "non-finite position");
+    for (int i = 0; i < nt; ++i)
+        if (!(tau_host[i] >= 0.0) || !std::isfinite(tau_host[i]))
+            return ctx->fail(MCMP2_EINVAL, "imaginary times must be finite and >= 0");
+    const Layout &L = ctx->L;
+    cudaStream_t st = ctx->stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    double *sr = ctx->at<double>(L.stage_r), *stau = ctx->at<double>(L.stage_tau);
+    CK(cudaMemcpyAsync(sr, r_host, sizeof(double) * m * 6, cudaMemcpyHostToDevice, st), "copy positions");
+    CK(cudaMemcpyAsync(stau, tau_host, sizeof(double) * nt, cudaMemcpyHostToDevice, st), "copy times");
+    CK(cudaMemsetAsync(ctx->ws + L.elements, 0, need * sizeof(double), st), "clear element record");
+    DebugTile dbg;
+    dbg.out = ctx->at<double>(L.elements);
+    dbg.bp = bp;
+    dbg.bq = bq;
+    double *slot = ctx->at<double>(L.per_step);
+    const int rc = step_integrand(ctx, sr, stau, 0, slot, 0, false, false, nullptr, nullptr, dbg);
+    if (rc) return rc;
+    double step = 0.0;
+    CK(cudaMemcpyAsync(out_host, dbg.out, need * sizeof(double), cudaMemcpyDeviceToHost, st), "copy elements");
+    CK(cudaMemcpyAsync(&step, slot, sizeof(double), cudaMemcpyDeviceToHost, st), "copy step");
+    CK(cudaStreamSynchronize(st), "element record sync");
+    if (ctx->precision != MCMP2_FP64) {
+        const int rc2 = mixed_check_flag(ctx->L.mixed, ctx->ws, st, ctx->err);
+        if (rc2) return rc2;
+    }
+    if (step_host) *step_host = step;
     return MCMP2_OK;
 }
 

@@ -43,9 +43,10 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
 // spinor formation with the scaled split planes of every time, and the
 // contraction writing partials [n_tau][n_tiles].  ev (if non-null) gets
 // ev[0], ev[1] recorded around the contraction launch.
+// dbg (optional) records the per-element values of one tile.
 int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *ws, const double *r,
                const float *scale, const double *a, double *partials, cudaStream_t st, std::string &err,
-               cudaEvent_t *ev, int *n_launches, int *n_pair_launches);
+               cudaEvent_t *ev, int *n_launches, int *n_pair_launches, const DebugTile &dbg = DebugTile{});
 
 // Reads (synchronously) and clears the device flag a timed-out kernel sets.
 int mixed_check_flag(const MixedLayout &L, char *ws, cudaStream_t st, std::string &err);

@@ -25,6 +25,8 @@ double *g_partials_addr[MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device, looked up once
 // per device (host code only sees a host-side stand-in under the array's name).
+// The cached address is not refreshed: a device reset after the first call on
+// that device is not supported (the header says so).
 int scratch_address(double **out)
 {
     int dev = -1;
@@ -45,11 +47,12 @@ extern "C" int mcmp2_pair_sum_f64_noalloc(int m, int n_occ, int n_vir, int n_tau
                                           const double *scale, const double *a, double lambda, double *out,
                                           void *cuda_stream)
 {
-    if (m < 2 || n_occ < 1 || n_vir < 1 || n_tau < 1 || m > (1 << 20) || n_occ + n_vir > 65536 || !phi ||
-        !scale || !a || !out || !(lambda > 0.0) || lambda == __builtin_inf())
+    if (m < 2 || n_occ < 1 || n_vir < 1 || n_tau < 1 || m > mcmp2::MAX_WALKER_PAIRS || n_tau > mcmp2::MAX_TAU ||
+        n_occ + n_vir > 65536 || !phi || !scale || !a || !out || !(lambda > 0.0) || lambda == __builtin_inf())
         return MCMP2_EINVAL;
-    const int n_tiles = mcmp2::n_tiles_for(m, mcmp2::TILE_PAIRS_F64);
-    if ((size_t)n_tiles * (size_t)n_tau > NOALLOC_MAX_PARTIALS) return MCMP2_ENOSPACE;
+    // 64-bit count (at most 8.4e6 tiles for the largest m), checked before any narrowing.
+    const long long n_tiles = mcmp2::n_tiles_for(m, mcmp2::TILE_PAIRS_F64);
+    if ((unsigned long long)n_tiles * (unsigned long long)n_tau > NOALLOC_MAX_PARTIALS) return MCMP2_ENOSPACE;
     double *partials = nullptr;
     const int rc = scratch_address(&partials);
     if (rc != MCMP2_OK) return rc;
@@ -67,7 +70,7 @@ extern "C" int mcmp2_pair_sum_f64_noalloc(int m, int n_occ, int n_vir, int n_tau
     auto *red = reinterpret_cast<mcmp2::ReduceScratch *>(partials + NOALLOC_MAX_PARTIALS);
     if (cudaMemsetAsync(&red->done, 0, sizeof(red->done), st) != cudaSuccess) return MCMP2_ECUDA;
     if (mcmp2::launch_pairs_f64(s, phi, scale, a, partials, st) != cudaSuccess) return MCMP2_ECUDA;
-    if (mcmp2::launch_reduce(s, partials, n_tiles, out, nullptr, 0, nullptr, red, st) != cudaSuccess)
+    if (mcmp2::launch_reduce(s, partials, (int)n_tiles, out, nullptr, 0, nullptr, red, st) != cudaSuccess)
         return MCMP2_ECUDA;
     return MCMP2_OK;
 }

@@ -273,7 +273,8 @@ _SOFT_SIZE_CL = [(0, 0.1, 1.3, 8), (1, 0.1, 1.3, 5)]
 
 
 def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = False,
-                small_scale: float | None = None, two_component: bool = False) -> System:
+                small_scale: float | None = None, two_component: bool = False,
+                weights: dict | None = None) -> System:
     """Draw one of the synthetic systems.
 
     config: "tiny" (Z=30 + Z=1, n_L = 20, 4 occ / 16 vir),
@@ -288,7 +289,9 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     of the size of the Coulomb ones.
     two_component: two-component spinors (alpha, beta) over the large basis
     only, orthonormal in S_LL; C keeps 4 n_L rows with the small rows zero and
-    the system is marked n_comp = 2."""
+    the system is marked n_comp = 2.
+    weights: optional {Z: (c1, zeta1, c2, zeta2)} replacing the weight-function
+    parameters of those nuclear charges (the spinors and energies are unchanged)."""
     rng = np.random.default_rng(seed)
     charges, centres = _geometry(config, n_units)
     shells = []
@@ -349,7 +352,7 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     C[:, 1::2] = time_reversed_coefficients(half, n_l)
     C = _loewdin(C, metric)
 
-    weight = np.array([TABLE1[TABLE1_ROW_FOR_Z[z_]] for z_ in charges], dtype=np.float64)
+    weight = np.array([(weights or {}).get(z_, TABLE1[TABLE1_ROW_FOR_Z[z_]]) for z_ in charges], dtype=np.float64)
     name = config if config != "size" else f"size{n_units}"
     if soft:
         name += "-soft"

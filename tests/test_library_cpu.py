@@ -65,3 +65,28 @@ def test_null_context_calls_return_einval(lib):
     assert lib.mcmp2_eval_fixed(None, 1, None, None, None) == -1
     assert lib.mcmp2_last_error(None) == b"null context"
     lib.mcmp2_destroy(None)
+
+
+@pytest.mark.parametrize("m,n_tau,code", [
+    (1 << 20, 1, -1),   # beyond the largest m any entry point accepts (65536)
+    (65537, 1, -1),
+    (65536, 1, -6),     # 33.6e6 tiles of 8 pairs: far beyond the fixed scratch array
+    (1024, 65, -1),     # more times than a context accepts
+    (1024, 8, -6),      # 8,256 tiles x 8 times > 65,536 partial sums
+    (1, 1, -1),
+])
+def test_noalloc_size_checks_come_before_any_device_work(lib, m, n_tau, code):
+    """The allocation-free call rejects its sizes on the host (64-bit tile counts) before it
+    touches a device, so these calls need no GPU; the pointers are never dereferenced."""
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    rc = lib.mcmp2_pair_sum_f64_noalloc(m, 4, 16, n_tau, p, p, p, 1.0, p, None)
+    assert rc == code
+
+
+def test_dims_limits_match_the_header(lib):
+    n = ctypes.c_size_t(0)
+    ok = B.Dims(2, 20, 4, 16, 65536, 64)
+    assert lib.mcmp2_workspace_bytes(ctypes.byref(ok), 0, ctypes.byref(n)) == 0
+    for bad in (B.Dims(2, 20, 4, 16, 65537, 1), B.Dims(2, 20, 4, 16, 16, 65)):
+        assert lib.mcmp2_workspace_bytes(ctypes.byref(bad), 0, ctypes.byref(n)) == -1

@@ -108,7 +108,7 @@ def test_cartesian_functions_follow_their_definition(tiny, tiny_oracle):
 
 
 def test_small_components_are_sigma_dot_grad_of_the_small_coefficients(tiny, tiny_oracle):
-    """Eq. KB: phi^S = i(sigma.p) chi = (sigma.grad) chi with chi = sum_mu C^S_mu g_mu e_s,
+    """Kinetic balance (after Eq. C): phi^S = i(sigma.p) chi = (sigma.grad) chi with chi = sum_mu C^S_mu g_mu e_s,
     checked by finite differences of chi built from basis values only."""
     n_l = tiny.n_l
     sig = mp2.PAULI

@@ -1,9 +1,10 @@
-"""The allocation-free entry point against the regular replay entry point.
+"""The allocation-free entry point against the regular replay entry point and the oracle.
 
 Callers that cannot allocate device memory use mcmp2_pair_sum_f64_noalloc,
 whose intermediate sums live in a fixed array inside the library; it must
 give the same step estimate as mcmp2_eval_fixed (FP64 form) for the same
-samples, call after call.
+samples, call after call, and both must be the oracle's I'_n of Eq. redundant
+(oracle.eval_steps) to the FP64 parity tolerance.
 """
 import numpy as np
 import pytest
@@ -40,7 +41,8 @@ def test_noalloc_matches_replay_on_two_calls(tiny, tiny_oracle, m, n_tau):
     r = synthetic.walker_positions(tiny.centres, 2, m, seed=600 + m)
     tau = synthetic.imaginary_times(tiny_oracle.lam(), 2, n_tau, seed=601 + m)
     ctx = pkg.Context(tiny, m, n_tau, pkg.MCMP2_FP64)
-    want, absmean = ctx.eval_fixed(r, tau), tiny_oracle.eval_steps(r, tau, with_abs=True)[1]
+    replay = ctx.eval_fixed(r, tau)
+    want, absmean = tiny_oracle.eval_steps(r, tau, with_abs=True)
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     for k in range(2):  # two calls in a row, different samples
         phi, scale, a = _inputs(tiny, tiny_oracle, r[k], tau[k])
@@ -48,7 +50,8 @@ def test_noalloc_matches_replay_on_two_calls(tiny, tiny_oracle, m, n_tau):
         torch.cuda.synchronize()
         got = float(out.item())
         scale_k = max(abs(want[k]), 1e-3 * absmean[k])
-        assert abs(got - want[k]) <= REL * scale_k, (k, got, want[k])
+        assert abs(got - want[k]) <= REL * scale_k, (k, got, want[k])      # the oracle
+        assert abs(got - replay[k]) <= REL * scale_k, (k, got, replay[k])  # the regular entry point
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(tiny, tiny_oracle):
