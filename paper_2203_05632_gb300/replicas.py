@@ -13,6 +13,9 @@ holds the host-side bookkeeping:
 * ``gather_and_combine`` — collect every rank's result over a
   ``torch.distributed`` process group at the end of a run and combine them.
   Ranks that failed pass ``None`` and are left out.
+* ``spawn_local`` — start N local ranks (one process per GPU) of a command
+  with the torch.distributed environment set, for a run that was not started
+  by a launcher;
 * ``write_result`` / ``combine_directory`` — the fault-tolerant path: each
   replica writes its result file atomically when it finishes (or at each
   checkpoint); the combination reads whatever the surviving replicas wrote,
@@ -23,6 +26,8 @@ from __future__ import annotations
 import json
 import math
 import os
+import socket
+import subprocess
 
 
 def combine(results):
@@ -106,3 +111,32 @@ def combine_directory(directory):
     out = combine(results.values())
     out["replicas"] = sorted(results)
     return out
+
+
+def free_port() -> int:
+    """A free TCP port on 127.0.0.1 for the rendezvous of local ranks."""
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def spawn_local(n_ranks: int, cmd, timeout=None):
+    """Run `cmd` (an argv list) as n_ranks local processes, rank r with RANK = LOCAL_RANK = r,
+    WORLD_SIZE = n_ranks and a rendezvous on 127.0.0.1 (one process per GPU, the replicas
+    of the paper's parallel scheme).  Standard output and error are inherited.  Returns
+    the exit codes in rank order; a rank still running after `timeout` seconds is killed
+    (its exit code is then negative)."""
+    port = free_port()
+    procs = []
+    for r in range(n_ranks):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(n_ranks),
+                   LOCAL_WORLD_SIZE=str(n_ranks), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen(list(cmd), env=env))
+    codes = []
+    for p in procs:
+        try:
+            codes.append(p.wait(timeout=timeout))
+        except subprocess.TimeoutExpired:
+            p.kill()
+            codes.append(p.wait())
+    return codes

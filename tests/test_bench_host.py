@@ -43,3 +43,45 @@ def test_traffic_figures_come_from_the_committed_summaries(key, profile):
 
 def test_traffic_table_has_only_captured_instances():
     assert set(bench.PAIRS_TRAFFIC_BYTES) == {("mixed", 4), ("tf32", 4), ("mixed", 2)}
+
+
+def test_two_local_ranks_print_one_line_with_the_combined_replicas(capfd):
+    """bench.py's multi-replica path on CPU: two ranks started by replicas.spawn_local (the
+    path `bench.py --gpus 2` takes without a launcher), a gloo process group, the max over
+    ranks of the timed region and the inverse-variance combination of the replicas'
+    results (Sec. III); the GPU work is a stand-in (tests/bench_rank_stand_in.py)."""
+    import json
+    import math
+    import sys
+
+    from paper_2203_05632_gb300 import replicas
+    helper = os.path.join(ROOT, "tests", "bench_rank_stand_in.py")
+    codes = replicas.spawn_local(2, [sys.executable, helper, "--gpus", "2", "--steps", "5", "--warmup", "3"],
+                                 timeout=300)
+    assert codes == [0, 0]
+    lines = [l for l in capfd.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1  # rank 0 alone prints
+    line = json.loads(lines[0])
+    assert line["n_gpus"] == 2 and line["steps"] == 5
+    assert line["ms_per_step"] == pytest.approx(20.0 / 5)  # the slower rank's 20 ms
+    assert line["value"] == pytest.approx(2 * 5 * 1000 / 0.020)  # whole job: both ranks' samples
+    assert line["e2e"]["value"] == pytest.approx(2 * 3 * 1000 / 1.5)
+    comb = line["replicas"]["combined"]
+    w0, w1 = 1 / 0.05 ** 2, 1 / 0.10 ** 2
+    assert comb["n_replicas"] == 2
+    assert comb["energy"] == pytest.approx((w0 * -1.0 + w1 * -1.1) / (w0 + w1))
+    assert comb["error"] == pytest.approx(1 / math.sqrt(w0 + w1))
+    assert [r["rank"] for r in line["replicas"]["per_rank"]] == [0, 1]
+
+
+def test_gpus_flag_starts_local_ranks_or_must_match_the_launcher(monkeypatch):
+    from paper_2203_05632_gb300 import replicas
+    calls = []
+    monkeypatch.setattr(replicas, "spawn_local", lambda n, cmd, timeout=None: calls.append((n, cmd)) or [0] * n)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    assert bench.main(["--gpus", "3", "--steps", "7"]) == 0
+    n, cmd = calls[0]
+    assert n == 3 and cmd[1].endswith("bench.py") and cmd[2:] == ["--gpus", "3", "--steps", "7"]
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.main(["--gpus", "3"]) == 2  # a launcher's world size that disagrees with --gpus
