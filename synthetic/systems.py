@@ -13,7 +13,9 @@ the same shapes:
   Loewdin-orthonormalised in the 4-component overlap metric;
 * orbital energies log-uniform in [-Z^2/2, -0.3] (occupied) and [0.1, 50]
   (virtual), equal within a Kramers pair;
-* weight-function parameters (c1, zeta1, c2, zeta2) per centre from Table 1.
+* weight-function parameters (c1, zeta1, c2, zeta2) per centre from Table 1,
+  or, for the nuclear charges Table 1 lacks (50 and 17), from the
+  weight-function scan (SCANNED_WEIGHTS).
 
 This module is an input generator only.  It evaluates no basis function or
 spinor at a point and contains none of the Monte Carlo MP2 arithmetic; the
@@ -47,8 +49,24 @@ TABLE1 = {
     "Au": (0.05, 0.6, 4.0, 0.8),
 }
 # Nuclear charges used by the synthetic clusters, mapped onto the nearest
-# Table 1 row (Z=17 takes the O row, Z=30 Cu, Z=50 Ag, Z=80 Au).
+# Table 1 row (Z=30 takes the Cu row, Z=80 Au, Z=1 H).
 TABLE1_ROW_FOR_Z = {1: "H", 17: "O", 30: "Cu", 50: "Ag", 80: "Au"}
+# Z = 50 and Z = 17 have no Table 1 row.  Their (c1, zeta1, c2, zeta2) were chosen
+# by the weight-function scan (paper_2203_05632_gb300/wscan.py) on the medium
+# system: the most diffuse exponent stays at 0.1, below twice the sum of the
+# smallest occupied and virtual exponents (0.05 each), so f^2/w decays at large
+# distance, and a second Gaussian of exponent 5 (Sn) or 3 (Cl) puts ~10 % of the
+# weight near the nuclei, where the occupied density is up to 10^5 times g of the
+# nearest Table 1 rows (Ag, O).  With them sigma-bar_N sqrt(N) stays within
+# 20 % from 10^4 to 4 x 10^4 steps; with the Ag and O rows it does not settle.
+SCANNED_WEIGHTS = {50: (0.5, 0.1, 1.0, 5.0), 17: (0.5, 0.1, 0.5, 3.0)}
+
+
+def weight_row(z: int):
+    """(c1, zeta1, c2, zeta2) of Eq. basisSet for nuclear charge z."""
+    if z in SCANNED_WEIGHTS:
+        return SCANNED_WEIGHTS[z]
+    return TABLE1[TABLE1_ROW_FOR_Z[z]]
 
 
 @dataclasses.dataclass
@@ -352,7 +370,7 @@ def make_system(config: str, seed: int = 2203, n_units: int = 1, soft: bool = Fa
     C[:, 1::2] = time_reversed_coefficients(half, n_l)
     C = _loewdin(C, metric)
 
-    weight = np.array([(weights or {}).get(z_, TABLE1[TABLE1_ROW_FOR_Z[z_]]) for z_ in charges], dtype=np.float64)
+    weight = np.array([(weights or {}).get(z_, weight_row(z_)) for z_ in charges], dtype=np.float64)
     name = config if config != "size" else f"size{n_units}"
     if soft:
         name += "-soft"

@@ -109,27 +109,6 @@ def test_tf32_and_bf16x3_forms_share_everything_but_the_contraction(tiny):
         assert abs(out[pkg.MCMP2_TF32][k] - out[pkg.MCMP2_MIXED][k]) <= _bound(orc, tiny, r[k], tau[k])
 
 
-def test_tf32_agrees_with_fp64_form_within_a_fifth_of_sigma():
-    """Same walk (FP64 sampling in both forms): the mean difference of the TF32 and FP64
-    step estimates is far below 0.2 sigma-bar of the FP64 run."""
-    medium = synthetic.make_system("medium")
-    m, n_tau, seed, n = 96, 2, 808, 400
-    r0 = synthetic.walker_positions(medium.centres, 1, m, seed=3)[0]
-    per = {}
-    for prec in (pkg.MCMP2_FP64, pkg.MCMP2_TF32):
-        ctx = pkg.Context(medium, m, n_tau, prec)
-        ctx.set_walkers(r0, seed, 100)
-        vals = []
-        for _ in range(n):
-            vals.append(ctx.run_steps(1, seed)["last_step"])
-        per[prec] = np.array(vals)
-        ctx.close()
-    d = per[pkg.MCMP2_TF32] - per[pkg.MCMP2_FP64]
-    I, s2, sb, nb = oracle.blocking(per[pkg.MCMP2_FP64])
-    assert nb == 4
-    assert abs(d.mean()) < 0.2 * sb, (d.mean(), sb)
-
-
 def test_tf32_walk_checkpoint_round_trip(tiny_soft):
     m, seed = 16, 21
     r0 = synthetic.walker_positions(tiny_soft.centres, 1, m, seed=2)[0]
