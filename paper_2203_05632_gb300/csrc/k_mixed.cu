@@ -114,26 +114,25 @@ constexpr int SP_EPI_WARPS = 8;                 // two per tensor-memory lane qu
 constexpr int SP_THREADS = 64 + 32 * SP_EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
 constexpr int SP_TMEM_COLS = 256;               // two 128-column accumulators
 constexpr int SP_MAX_TAU = 64;                  // scale staging capacity (the API limits n_tau to 64)
-constexpr int SP_ROW_BYTES = 272;               // staged half row: 2 chunks x 128 B + 16 B pad
-constexpr int SP_WARP_STAGE = 32 * SP_ROW_BYTES;  // 32 rows per epilogue warp
+constexpr int SP_BOX_BYTES = 32 * 128;          // one TMA store box: 32 rows x one 128-byte chunk
+constexpr int SP_WARP_STAGE = 2 * SP_BOX_BYTES;  // X and iX boxes of one epilogue warp
 constexpr int SP_BARS_OFF = SP_STAGES * SP_STAGE_BYTES;
 constexpr int SP_SCALE_OFF = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16;
-constexpr int SP_WSTAGE_OFF = SP_SCALE_OFF + SP_MAX_TAU * 64 * 4;
+constexpr int SP_WSTAGE_OFF = (SP_SCALE_OFF + SP_MAX_TAU * 64 * 4 + 1023) / 1024 * 1024;  // swizzled boxes: 1 KB aligned
 constexpr int SP_SMEM = SP_WSTAGE_OFF + SP_EPI_WARPS * SP_WARP_STAGE + 1024;
 static_assert(SP_SMEM <= 232448, "spinor kernel exceeds the shared memory of one CTA");
 
 struct SpinorMaps {
-    CUtensorMap m[8];  // 0..3: A_L hi, A_L lo, B_L hi, B_L lo; 4..7: the same for the gradient part
+    CUtensorMap m[12];  // 0..3: A_L hi, A_L lo, B_L hi, B_L lo; 4..7: the same for the gradient part;
+                        // 8, 9: X occupied / virtual (stores); 10, 11: iX occupied / virtual (stores)
 };
 
+// The operand rows X [n_tau][rows][k_pad / 16][128 B] (occupied and virtual) and
+// i X (planes -im, re) are written through the store tensor maps of SpinorMaps.
 struct SpinorArgs {
     const float *scale;   // [n_tau][n_orb]
-    __nv_bfloat16 *occ;   // [n_tau][rows][k_occ_pad / 16][128 B]
-    __nv_bfloat16 *vir;   // [n_tau][rows][k_vir_pad / 16][128 B]
-    __nv_bfloat16 *iocc;  // i X in the same layout (planes -im, re)
-    __nv_bfloat16 *ivir;
     int *abort_flag;
-    int P, nl, n_mt, n_kb, n_kb_occ, n_occ, n_vir, n_orb, n_tau, rows, k_occ_pad, k_vir_pad;
+    int P, nl, n_mt, n_kb, n_kb_occ, n_occ, n_vir, n_orb, n_tau;
     int tf32;  // chunk = 16 re (TF32) + 16 im (TF32) instead of re_hi, re_lo, im_hi, im_lo (BF16)
     int ncomp; // spinor components: 4, or 2 (two-component systems: large components only, rows 2x + c)
 };
@@ -268,17 +267,23 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         }
     } else {
         // Epilogue: each lane owns one position row of the tile; the two warps of a
-        // lane quarter take orbitals 0-31 and 32-63 of the 64-orbital block.  For
-        // every time a warp stages its 32 rows x 32 orbitals in shared memory in the
-        // contraction's operand order (per 16-orbital chunk: re_hi, re_lo, im_hi,
-        // im_lo, 32 B each; or re, im as TF32, 64 B each), then writes the rows'
-        // 256-byte segments, two rows per store instruction.
+        // lane quarter take orbitals 0-31 and 32-63 (chunks 2 jh, 2 jh + 1) of the
+        // 64-orbital block.  A warp reads its accumulator columns (re and im of its 32
+        // orbitals for its 32 rows) from tensor memory once per tile and releases the
+        // buffer at once.  Then, for every time and chunk, it stages its 32 rows of the
+        // chunk in shared memory in the contraction's operand order (re_hi, re_lo,
+        // im_hi, im_lo, 32 B each; or re, im as TF32, 64 B each; 128-byte swizzle), and
+        // the same rows of iX = i X (halves swapped, the new first half negated), and
+        // one lane writes both 4 KB boxes with TMA stores.
         const int ew = warp - 2;
         const int quarter = warp & 3;
-        const int jh = ew >> 2;  // which 32 orbitals of the block
+        const int jh = ew >> 2;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
         float *sscale = reinterpret_cast<float *>(smem + SP_SCALE_OFF);  // [n_tau][64]
-        unsigned char *wstage = smem + SP_WSTAGE_OFF + ew * SP_WARP_STAGE;
+        unsigned char *sx = smem + SP_WSTAGE_OFF + ew * SP_WARP_STAGE;   // X box: 32 rows x 128 B
+        unsigned char *si = sx + SP_BOX_BYTES;                          // iX box
+        const uint32_t neg = args.tf32 ? 0x80000000u : 0x80008000u;    // sign bits of the packed values
+        const int sw = lane & 7;                                       // 128-byte swizzle of this lane's row
         int buf = 0;
         uint32_t ephase[2] = {0, 0};
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -288,36 +293,43 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             if (bar_any<1, 32 * SP_EPI_WARPS>(!got)) break;  // also: every epilogue warp is done with the previous scales
             ephase[buf] ^= 1u;
             fence_after();
+            float re[2][16], im[2][16];
+            tmem_ld<16>(lane_addr + 128u * buf + 32u * jh, re[0]);
+            tmem_ld<16>(lane_addr + 128u * buf + 32u * jh + 16u, re[1]);
+            tmem_ld<16>(lane_addr + 128u * buf + 64u + 32u * jh, im[0]);
+            tmem_ld<16>(lane_addr + 128u * buf + 64u + 32u * jh + 16u, im[1]);
+            tmem_wait_ld();
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);  // the accumulator is in registers: MMAs may reuse it
+            buf ^= 1;
             const bool occ = kb < args.n_kb_occ;
             const int kl = occ ? kb : kb - args.n_kb_occ;
-            const int kpad = occ ? args.k_occ_pad : args.k_vir_pad;
             const int k_first = (occ ? 0 : args.n_occ) + kl * 64;  // absolute index of the block's first orbital
             const int k_end = occ ? args.n_occ : args.n_orb;       // one past the region's last orbital
-            __nv_bfloat16 *planes = occ ? args.occ : args.vir;
-            __nv_bfloat16 *iplanes = occ ? args.iocc : args.ivir;
-            const uint32_t neg = args.tf32 ? 0x80000000u : 0x80008000u;  // sign bits of the packed values
-            const size_t time_elems = (size_t)args.rows * 4 * kpad;  // one time's operand rows
+            const CUtensorMap *mx = &maps.m[occ ? 8 : 9];
+            const CUtensorMap *mi = &maps.m[occ ? 10 : 11];
             for (int i = threadIdx.x - 64; i < 64 * args.n_tau; i += 32 * SP_EPI_WARPS) {
                 const int t = i >> 6, k = k_first + (i & 63);
                 sscale[i] = k < k_end ? args.scale[(size_t)t * args.n_orb + k] : 0.f;
             }
             bar_sync<1, 32 * SP_EPI_WARPS>();
-            for (int t = 0; t < args.n_tau; ++t) {
-                const float *st_ = sscale + 64 * t;
 #pragma unroll 1
-                for (int j = 2 * jh; j < 2 * jh + 2; ++j) {
-                    float re[16], im[16];
-                    tmem_ld<16>(lane_addr + 128u * buf + 16u * j, re);
-                    tmem_ld<16>(lane_addr + 128u * buf + 64u + 16u * j, im);
-                    tmem_wait_ld();
-                    uint4 *d = reinterpret_cast<uint4 *>(wstage + lane * SP_ROW_BYTES + 128 * (j - 2 * jh));
+            for (int t = 0; t < args.n_tau; ++t) {
+#pragma unroll
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int j = 2 * jh + jj;
+                    // A chunk past the region's last orbital is never read by the contraction.
+                    if (k_first + 16 * j >= k_end) continue;
+                    const float *st_ = sscale + 64 * t + 16 * j;
+                    uint4 d[8];
                     if (args.tf32) {
                         uint32_t rt[16], it[16];
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const float sc = st_[16 * j + i];
-                            rt[i] = to_tf32(re[i] * sc);
-                            it[i] = to_tf32(im[i] * sc);
+                            const float sc = st_[i];
+                            rt[i] = to_tf32(re[jj][i] * sc);
+                            it[i] = to_tf32(im[jj][i] * sc);
                         }
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
@@ -328,9 +340,9 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                         uint32_t rh[8], rl[8], ih[8], il[8];
 #pragma unroll
                         for (int i = 0; i < 16; i += 2) {
-                            const float s0 = st_[16 * j + i], s1 = st_[16 * j + i + 1];
-                            const float xr0 = re[i] * s0, xr1 = re[i + 1] * s1;
-                            const float xi0 = im[i] * s0, xi1 = im[i + 1] * s1;
+                            const float s0 = st_[i], s1 = st_[i + 1];
+                            const float xr0 = re[jj][i] * s0, xr1 = re[jj][i + 1] * s1;
+                            const float xi0 = im[jj][i] * s0, xi1 = im[jj][i + 1] * s1;
                             const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
                             const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
                             rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
@@ -347,40 +359,35 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                         d[6] = make_uint4(il[0], il[1], il[2], il[3]);
                         d[7] = make_uint4(il[4], il[5], il[6], il[7]);
                     }
-                }
-                __syncwarp();
-                // Each row's 256 bytes (two chunks), 16 per lane, to X; and to iX = i X, whose
-                // chunk holds -im then re: piece p of a chunk comes from piece p ^ 4, negated
-                // in the first half.
-                const int half = lane >> 4, piece = lane & 15;
-                const int ipiece = (piece & 8) | ((piece & 7) ^ 4);
-                const uint32_t flip = (piece & 4) ? 0u : neg;
-                // Chunks past the region's last orbital are never read by the contraction.
-                const bool real_chunk = k_first + 16 * (2 * jh + (piece >> 3)) < k_end;
-#pragma unroll 4
-                for (int it = 0; it < 16; ++it) {
-                    const int row = 2 * it + half;
-                    const int x = mt * 128 + 32 * quarter + row;
-                    if (x < args.P && real_chunk) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * piece);
-                        uint4 w = *reinterpret_cast<const uint4 *>(wstage + row * SP_ROW_BYTES + 16 * ipiece);
-                        w.x ^= flip;
-                        w.y ^= flip;
-                        w.z ^= flip;
-                        w.w ^= flip;
-                        const size_t off = (size_t)t * time_elems + (size_t)(args.ncomp * x + c4) * (4 * kpad) +
-                                           kl * 256 + jh * 128 + 8 * piece;
-                        *reinterpret_cast<uint4 *>(planes + off) = v;
-                        *reinterpret_cast<uint4 *>(iplanes + off) = w;
+                    // The previous boxes must have been read out before they are overwritten.
+                    if (lane == 0) bulk_wait_read_all();
+                    __syncwarp();
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const int u = (v ^ sw) << 4;  // 128-byte swizzle: 16-byte unit v of row `lane`
+                        uint4 w = d[v ^ 4];
+                        const uint32_t f = v < 4 ? neg : 0u;
+                        w.x ^= f;
+                        w.y ^= f;
+                        w.z ^= f;
+                        w.w ^= f;
+                        *reinterpret_cast<uint4 *>(sx + lane * 128 + u) = d[v];
+                        *reinterpret_cast<uint4 *>(si + lane * 128 + u) = w;
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    const int x0 = kl * 256 + 64 * j, y0 = mt * 128 + 32 * quarter;
+                    if (lane == 0 && y0 < args.P) {
+                        // Box {64 elements, 1 component, 32 positions, 1 time}; positions past P are clipped.
+                        tma_store_4d(mx, sx, x0, c4, y0, t);
+                        tma_store_4d(mi, si, x0, c4, y0, t);
+                        bulk_commit();
                     }
                 }
-                __syncwarp();
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
-            buf ^= 1;
         }
+        if (lane == 0) bulk_wait_all();  // every store of this warp has reached global memory
+        __syncwarp();
     }
     fence_before();
     __syncthreads();
@@ -1415,6 +1422,33 @@ int encode(void *out, void *addr, int rank, const cuuint64_t *dims, const cuuint
     return MCMP2_OK;
 }
 
+// 4-D BF16 tensor map of one operand-row array for the spinor kernel's TMA stores:
+// dims (element of a row, component, position, time), box {64, 1, 32, 1} = one
+// 128-byte chunk of 32 positions' rows, 128-byte swizzle.
+int encode_store(void *out, void *addr, int kpad, int ncomp, int P, int rows, int n_tau, std::string &err)
+{
+    auto enc = encode_fn();
+    if (!enc) {
+        err = "cuTensorMapEncodeTiled is not available from the driver";
+        return MCMP2_EUNSUPPORTED;
+    }
+    const cuuint64_t row_bytes = (cuuint64_t)4 * kpad * 2;
+    const cuuint64_t dims[4] = {(cuuint64_t)4 * kpad, (cuuint64_t)ncomp, (cuuint64_t)P, (cuuint64_t)n_tau};
+    const cuuint64_t strides[3] = {row_bytes, row_bytes * ncomp, row_bytes * rows};
+    const cuuint32_t box[4] = {64u, 1u, 32u, 1u};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMap map;
+    const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, addr, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        err = "cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")";
+        return MCMP2_ECUDA;
+    }
+    std::memcpy(out, &map, sizeof(map));
+    return MCMP2_OK;
+}
+
 }  // namespace
 
 MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t offset)
@@ -1521,6 +1555,16 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
     // a two-component system fills the first 4m of the 8m rows of each time.
     plan.ncomp = s.n_comp == 2 ? 2 : 4;
     const int rows_used = 2 * plan.ncomp * s.m;
+    // The spinor kernel's stores of those rows, row ncomp x + c of position x and component c.
+    if ((rc = encode_store(plan.maps_spinor[8], ws + L.occ_planes, L.k_occ_pad, plan.ncomp, L.P, L.rows, L.n_tau,
+                           err)) ||
+        (rc = encode_store(plan.maps_spinor[9], ws + L.vir_planes, L.k_vir_pad, plan.ncomp, L.P, L.rows, L.n_tau,
+                           err)) ||
+        (rc = encode_store(plan.maps_spinor[10], ws + L.occ_iplanes, L.k_occ_pad, plan.ncomp, L.P, L.rows, L.n_tau,
+                           err)) ||
+        (rc = encode_store(plan.maps_spinor[11], ws + L.vir_iplanes, L.k_vir_pad, plan.ncomp, L.P, L.rows, L.n_tau,
+                           err)))
+        return rc;
     {
         const cuuint64_t dO[3] = {(cuuint64_t)4 * L.k_occ_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
         const cuuint64_t sO[2] = {(cuuint64_t)L.k_occ_pad * 8, (cuuint64_t)L.rows * L.k_occ_pad * 8};
@@ -1602,9 +1646,8 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     SpinorMaps smaps;
     std::memcpy(&smaps, plan.maps_spinor, sizeof(smaps));
     const int n_mt = (L.P + 127) / 128;
-    SpinorArgs sa{scale, bf(L.occ_planes), bf(L.vir_planes), bf(L.occ_iplanes), bf(L.vir_iplanes), flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ,
-                  s.n_occ, s.n_vir, s.n_orb, s.n_tau, L.rows, L.k_occ_pad, L.k_vir_pad, plan.tf32 ? 1 : 0,
-                  plan.ncomp};
+    SpinorArgs sa{scale, flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ, s.n_occ, s.n_vir, s.n_orb, s.n_tau,
+                  plan.tf32 ? 1 : 0, plan.ncomp};
     const int sp_tiles = n_mt * plan.ncomp * L.n_kb;
     spinor_mixed_kernel<<<sp_tiles < sms ? sp_tiles : sms, SP_THREADS, SP_SMEM, st>>>(smaps, sa);
 

@@ -21,13 +21,13 @@ struct MixedLayout {
     size_t end;
 };
 
-// Host-side state: tensor maps (8 for spinor formation, 4 for the contraction).
+// Host-side state: tensor maps (12 for spinor formation, 4 for the contraction).
 struct MixedPlan {
     bool ready = false;
     bool tf32 = false;  // propagator operands as TF32 (re, im) instead of split BF16 (re hi/lo, im hi/lo)
     int ncomp = 4;      // spinor components of the loaded system (2: 32-pair tiles of 2 x 2 blocks)
     unsigned long long withhold_once_ns = 0;  // test hook for the bounded-wait path (see mcmp2_test_stall_next)
-    alignas(64) unsigned char maps_spinor[8][128];
+    alignas(64) unsigned char maps_spinor[12][128];  // 8 loads of spinor formation, 4 stores of X and i X
     int pair_clusters = 0;  // CTA pairs of the contraction resident at once (its persistent grid)
     alignas(64) unsigned char maps_pairs[4][128];  // X and i X, occupied and virtual
 };
