@@ -448,6 +448,10 @@ constexpr int PR_STAGE_BYTES = 2 * PR_TILE_BYTES;   // A chunk, then this CTA's 
 constexpr int PR_GROUPS = 2;
 constexpr int PR_GROUP_WARPS = 8;                   // two per tensor-memory lane quarter
 constexpr int PR_EPI_WARPS = PR_GROUPS * PR_GROUP_WARPS;
+constexpr int PR_QHALVES = PR_GROUP_WARPS / 4;      // warps of a group per tensor-memory lane quarter
+constexpr int PR_QW4 = 16 / PR_QHALVES;             // q-pairs per warp and item, four-component tiles
+constexpr int PR_QW2 = 32 / PR_QHALVES;             // q-pairs per warp and item, two-component tiles
+static_assert(PR_GROUP_WARPS % 4 == 0 && 16 % PR_QHALVES == 0, "a group covers the four lane quarters");
 constexpr int PR_THREADS = 64 + 32 * PR_EPI_WARPS;
 constexpr int PR_TMEM_COLS = 512;                   // per group: re | im of 128 columns
 constexpr int PR_GM_BYTES = 16 * 3 * 128 * 8;       // G- like blocks of one item: 48 KB
@@ -808,7 +812,7 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
     const int g = ew / PR_GROUP_WARPS;
     const int gw = ew - g * PR_GROUP_WARPS;
     const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
-    const int qhalf = gw >> 2;     // q-pairs 8*qhalf .. +7 of the tile
+    const int qhalf = gw >> 2;     // q-pairs PR_QW4*qhalf .. +PR_QW4-1 of the tile
     const int row = 32 * quarter + lane;
     const int p_local = row >> 3, e = (row >> 2) & 1, c = lane & 3;
     const int gbase = lane & ~7;
@@ -828,8 +832,8 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
         if (group_any(g, !got_m)) break;  // the group leaves together
         fence_after();
 #pragma unroll 1
-        for (int qb = 0; qb < 4; ++qb) {
-            const int q0 = 8 * qhalf + 2 * qb;
+        for (int qb = 0; qb < PR_QW4 / 2; ++qb) {
+            const int q0 = PR_QW4 * qhalf + 2 * qb;
             float vr[16], vi[16];
             tmem_ld<16>(lane_addr + 8u * q0, vr);
             tmem_ld<16>(lane_addr + 128u + 8u * q0, vi);
@@ -873,8 +877,8 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
         if constexpr (INTER != MCMP2_COULOMB) {
             // One q-pair per tensor-memory load: the operator terms hold more state per q.
 #pragma unroll 1
-            for (int qi = 0; qi < 8; ++qi) {
-                const int ql = 8 * qhalf + qi;
+            for (int qi = 0; qi < PR_QW4; ++qi) {
+                const int ql = PR_QW4 * qhalf + qi;
                 float gpr[8], gpi[8];
                 tmem_ld<8>(lane_addr + 8u * ql, gpr);
                 tmem_ld<8>(lane_addr + 128u + 8u * ql, gpi);
@@ -905,8 +909,8 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
             }
         }
 #pragma unroll 1
-        for (int qb = 0; qb < (INTER == MCMP2_COULOMB ? 4 : 0); ++qb) {
-            const int q0 = 8 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
+        for (int qb = 0; qb < (INTER == MCMP2_COULOMB ? PR_QW4 / 2 : 0); ++qb) {
+            const int q0 = PR_QW4 * qhalf + 2 * qb;  // two q-pairs per tensor-memory load
             float gpr[16], gpi[16];
             tmem_ld<16>(lane_addr + 8u * q0, gpr);
             tmem_ld<16>(lane_addr + 128u + 8u * q0, gpi);
@@ -991,7 +995,7 @@ __device__ __forceinline__ void pairs_epilogue_4c(const PairArgs &args, unsigned
         group_sync(g);
         if (gw == 0 && lane == 0 && bp <= bq) {
             double sum = 0.0;
-            for (int j = 0; j < 32; ++j) sum += red[j];
+            for (int j = 0; j < 16 * PR_QHALVES; ++j) sum += red[j];
             args.partials[(size_t)t * args.n_tiles + tile_index(bp, bq, args.nb)] = sum * args.inv_lambda;
         }
         group_sync(g);
@@ -1011,7 +1015,7 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
     const int g = ew / PR_GROUP_WARPS;
     const int gw = ew - g * PR_GROUP_WARPS;
     const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
-    const int qhalf = gw >> 2;     // q-pairs 16*qhalf .. +15 of the tile
+    const int qhalf = gw >> 2;     // q-pairs PR_QW2*qhalf .. +PR_QW2-1 of the tile
     const int row = 32 * quarter + lane;
     const int p_local = row >> 2, e = (row >> 1) & 1, c = lane & 1;
     const int gbase = lane & ~3;
@@ -1029,8 +1033,8 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
         if (group_any(g, !got_m)) break;
         fence_after();
 #pragma unroll 1
-        for (int qb = 0; qb < 4; ++qb) {
-            const int q0 = 16 * qhalf + 4 * qb;  // four q-pairs per tensor-memory load
+        for (int qb = 0; qb < PR_QW2 / 4; ++qb) {
+            const int q0 = PR_QW2 * qhalf + 4 * qb;  // four q-pairs per tensor-memory load
             float vr[16], vi[16];
             tmem_ld<16>(lane_addr + 4u * q0, vr);
             tmem_ld<16>(lane_addr + 128u + 4u * q0, vi);
@@ -1059,8 +1063,8 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
         const double a_lane = q_lane < args.m ? args.a[q_lane] : 0.0;
         double acc = 0.0;
 #pragma unroll 1
-        for (int qb = 0; qb < 4; ++qb) {
-            const int q0 = 16 * qhalf + 4 * qb;
+        for (int qb = 0; qb < PR_QW2 / 4; ++qb) {
+            const int q0 = PR_QW2 * qhalf + 4 * qb;
             float gpr[16], gpi[16];
             tmem_ld<16>(lane_addr + 4u * q0, gpr);
             tmem_ld<16>(lane_addr + 128u + 4u * q0, gpi);
@@ -1128,7 +1132,7 @@ __device__ __forceinline__ void pairs_epilogue_2c(const PairArgs &args, unsigned
         group_sync(g);
         if (gw == 0 && lane == 0 && bp <= bq) {
             double sum = 0.0;
-            for (int j = 0; j < 64; ++j) sum += red[j];
+            for (int j = 0; j < 32 * PR_QHALVES; ++j) sum += red[j];
             args.partials[(size_t)t * args.n_tiles + tile_index(bp, bq, args.nb)] = sum * args.inv_lambda;
         }
         group_sync(g);
