@@ -35,8 +35,11 @@ summand.  The model used instead is first-order probabilistic error analysis
  * the FP32 trace arithmetic of the epilogue adds at most
    u_epi sum_AB |c_A c_B| (|direct| + |exchange|) a_p a_q / lambda.
 
-A test then accepts |got - want| <= KAPPA sigma + epilogue term.  Only the test
-suite and the smoke check use this module.
+A test then accepts |got - want| <= KAPPA sigma + epilogue term.  For a sum of
+summands (a step estimate, a tile's partial sum) the operand errors of a walker
+pair's positions are shared by every summand using the pair, so the sum is
+linearised as a whole (sum_model).  Only the test suite and the smoke check use
+this module.
 """
 from __future__ import annotations
 
@@ -141,6 +144,13 @@ class TileSetup:
                             np.stack([phi[q][0] for q in Q]), np.stack([phi[q][1] for q in Q])])
         self.NR = np.stack([np.stack([nrm[p][0] for p in P]), np.stack([nrm[p][1] for p in P]),
                             np.stack([nrm[q][0] for q in Q]), np.stack([nrm[q][1] for q in Q])])
+        # The same per walker pair (positions shared by several summands): [U][2][n_orb][4]
+        # and each summand's (p, q) as indices into it.
+        where = {p: i for i, p in enumerate(idx)}
+        self.PHU = np.stack([np.stack(phi[p]) for p in idx])
+        self.NRU = np.stack([np.stack(nrm[p]) for p in idx])
+        self.ip = np.array([where[p] for p in P])
+        self.iq = np.array([where[q] for q in Q])
         self.w = np.array([a[p] * a[q] / lam for p, q in pairs])
         self.OA = np.stack([_operators(unit[p], interaction)[0] for p in P])  # [B][nA][4][4]
         self.OB = np.stack([_operators(unit[q], interaction)[0] for q in Q])
@@ -219,12 +229,60 @@ def element_model(orc, r_step, tau_step, pairs, form: Form, interaction: int = 0
     return vals, sig, epi
 
 
+def sum_model(orc, r_step, tau_step, pairs, form: Form, interaction: int = 0):
+    """(sigma, epi) per time of the SUM of the listed summands.  The operand errors of a
+    walker pair's two positions are shared by every summand that uses the pair, so the
+    sum is linearised as a whole (derivatives with respect to the per-position operands);
+    the propagator-entry terms (FP32 accumulation, parking) belong to one summand each and
+    add in quadrature; the epilogue terms add linearly."""
+    import torch
+
+    ts = TileSetup(orc, r_step, pairs, interaction)
+    n_occ = ts.n_occ
+    sig = np.zeros(len(tau_step))
+    epi = np.zeros(len(tau_step))
+    for t, tau in enumerate(tau_step):
+        s = ts.scales(tau)[None, None, :, None]
+        XU = ts.PHU * s  # [U][2][n_orb][4]
+        SXU = np.sqrt((form.u_gemm * ts.NRU * s) ** 2 + (form.u_rep * np.abs(XU)) ** 2)
+        XUt = torch.tensor(XU, requires_grad=True)
+        X = torch.stack([XUt[ts.ip, 0], XUt[ts.ip, 1], XUt[ts.iq, 0], XUt[ts.iq, 1]])
+        e, G, mag = summands(ts, X, keep_graph=True)
+        e.sum().backward()
+        var = float(((XUt.grad.abs().numpy() * SXU) ** 2).sum())
+        Xn = X.detach().numpy()
+        for key, g in G.items():
+            ks = slice(0, n_occ) if key[0] == "m" else slice(n_occ, None)
+            x, y = {"m31": (2, 0), "m42": (3, 1), "p13": (0, 2), "p24": (1, 3), "p14": (0, 3), "p23": (1, 2)}[key]
+            norm2 = np.sqrt(np.einsum("bkc,bkd->bcd", np.abs(Xn[x][:, ks]) ** 2, np.abs(Xn[y][:, ks]) ** 2))
+            gg = g.grad.abs().numpy()
+            var += float(((gg * form.u_acc * norm2) ** 2).sum())
+            if key[0] == "m":
+                var += float(((gg * form.u_pack * np.abs(g.detach().numpy())) ** 2).sum())
+        sig[t] = np.sqrt(var)
+        epi[t] = form.u_epi * float(mag.detach().numpy().sum())
+    return sig, epi
+
+
 def step_tolerance(orc, r_step, tau_step, form: Form, interaction: int = 0) -> float:
-    """Tolerance of one step estimate I'_n, the mean of its summands: KAPPA times the
-    mean of their standard deviations (added linearly: summands that share a walker
-    pair share its operand errors) plus the mean epilogue term."""
+    """Tolerance of one step estimate I'_n = (1/n_tau) sum_t (1/mC2) sum_{p<q} e:
+    KAPPA times the model standard deviation of that mean (the sum linearised as a
+    whole, sum_model; the times are added linearly, since they share the spinor
+    values' errors) plus its epilogue terms."""
     m = r_step.shape[0]
     pairs = [(p, q) for p in range(m) for q in range(p + 1, m)]
-    _, sig, epi = element_model(orc, r_step, tau_step, pairs, form, interaction)
+    sig, epi = sum_model(orc, r_step, tau_step, pairs, form, interaction)
     n = len(pairs) * len(tau_step)
-    return KAPPA * sig.sum() / n + epi.sum() / n
+    return (KAPPA * sig.sum() + epi.sum()) / n
+
+
+def tile_tolerance(orc, r_step, tau_step, pairs, form: Form, interaction: int = 0):
+    """Tolerance of a sum of the listed summands, per time: KAPPA times the model standard
+    deviation of the sum (sum_model) plus its epilogue terms."""
+    sig, epi = sum_model(orc, r_step, tau_step, pairs, form, interaction)
+    return KAPPA * sig + epi
+
+
+def steps_tolerance(orc, r, tau, form: Form, interaction: int = 0):
+    """step_tolerance for each step of a replay (r [n][m][2][3], tau [n][n_tau])."""
+    return np.array([step_tolerance(orc, r[k], tau[k], form, interaction) for k in range(len(r))])

@@ -18,8 +18,7 @@ import synthetic
 from oracle import mp2
 
 from test_gpu_fp64 import _check_steps, _tile_index, _tile_pairs
-from test_gpu_mixed import _ok as _mixed_ok
-from test_gpu_tf32 import _bound as _tf32_bound
+from test_gpu_mixed import _steps_ok, _tile_ok
 
 pytestmark = pytest.mark.gpu
 
@@ -127,19 +126,14 @@ def test_two_component_long_walk_matches_deterministic_energy():
 @pytest.mark.parametrize("m,n_tau", [(16, 1), (13, 3), (2, 1), (33, 2), (70, 1)])
 def test_two_component_tensor_forms_match_oracle_tiny(tiny2c, tiny2c_oracle, prec, m, n_tau):
     """32 x 32-pair tiles of 2 x 2 blocks (ragged: m = 33, 70 span two and three
-    tile rows) within the bounds of the four-component tensor forms."""
+    tile rows) within the error model of each form."""
     n = 2
     r = synthetic.walker_positions(tiny2c.centres, n, m, seed=500 + m)
     tau = synthetic.imaginary_times(tiny2c_oracle.lam(), n, n_tau, seed=19 + m)
     ctx = pkg.Context(tiny2c, m, n_tau, prec)
     got = ctx.eval_fixed(r, tau)
-    want, absmean = tiny2c_oracle.eval_steps(r, tau, with_abs=True)
-    if prec == pkg.MCMP2_MIXED:
-        assert np.all(_mixed_ok(got, want, absmean)), (got, want)
-    else:
-        for k in range(n):
-            bound = _tf32_bound(tiny2c_oracle, tiny2c, r[k], tau[k])
-            assert abs(got[k] - want[k]) <= bound, (k, got[k], want[k], bound)
+    want = tiny2c_oracle.eval_steps(r, tau)
+    assert np.all(_steps_ok(tiny2c_oracle, r, tau, got, want, prec)), (got, want)
 
 
 def test_two_component_mixed_full_size_sampled_tiles(medium2c, medium2c_oracle):
@@ -158,7 +152,7 @@ def test_two_component_mixed_full_size_sampled_tiles(medium2c, medium2c_oracle):
         vals = medium2c_oracle.eval_pairs(r[0], tau[0], ps, qs)
         want = vals.sum(axis=0)
         got = partials[:, _tile_index(bp, bq, nb)]
-        assert np.all(_mixed_ok(got, want, np.abs(vals).sum(axis=0))), (bp, bq, got, want)
+        assert np.all(_tile_ok(medium2c_oracle, r[0], tau[0], ps, qs, got, want)), (bp, bq, got, want)
 
 
 @pytest.mark.parametrize("prec", [pkg.MCMP2_MIXED, pkg.MCMP2_TF32])

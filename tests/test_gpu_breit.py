@@ -2,20 +2,13 @@
 
 FP64 form: the parity bar of the Coulomb FP64 form, 1e-10 relative per step estimate
 (relative to max(|I'_n|, 1e-3 <|f|>)).  Tensor-core forms (split BF16 x3 and TF32, the
-operators applied to G- in the trace epilogue): the tolerance of the Coulomb operator in
-the same form, |got - want| <= REL |want| + ABS sum |f_pq| (REL = 2e-3, ABS = 1e-4 for
-split BF16 x3, whose products carry ~2^-16; both x 32 = 2^-11 / 2^-16 for TF32
-operands), with the absolute part scaled by sum_AB |c_A c_B| (6.25 Gaunt, 9 Breit):
-every operator combination is the Coulomb trace form of M_AB = O_A G- O_B, whose entries
-are entries of G- permuted and multiplied by unit phases (alpha_k), so each carries the
-Coulomb per-term error, weighted by |c_A c_B|.  (The worst-case bound from absolute
-expansions, 8 u |c_A c_B| times the traces of |O_A| |G-| |O_B| and |G+|, exceeds |I'_n|
-itself on these systems: the orbital sums cancel by three orders of magnitude.)  Plus a
-walk on a system with order-one small components against the deterministic Coulomb +
-Gaunt MP2 energy (P4 with the Gaunt term), split BF16 against the FP64 form on one walk
-(within a fifth of sigma-bar), and the guards: the adjoint keeps the Coulomb operator,
-two-component systems have no small components for it, and checkpoints record the
-interaction.
+operators applied to G- in the trace epilogue): the error model of each form
+(oracle/bounds.py) with the operator traces, summed over the summands of a step or of a
+tile (the per-summand comparison is in test_gpu_elements.py).  Plus a walk on a system
+with order-one small components against the deterministic Coulomb + Gaunt MP2 energy (P4
+with the Gaunt term), split BF16 against the FP64 form on one walk (within a fifth of
+sigma-bar), and the guards: the adjoint keeps the Coulomb operator, two-component systems
+have no small components for it, and checkpoints record the interaction.
 """
 import numpy as np
 import pytest
@@ -23,7 +16,7 @@ import pytest
 import oracle
 import paper_2203_05632_gb300 as pkg
 import synthetic
-from oracle import mp2
+from oracle import bounds, mp2
 
 pytestmark = pytest.mark.gpu
 
@@ -37,13 +30,12 @@ def _ok(got, want, absmean):
     return np.abs(got - want) <= 1e-10 * np.maximum(np.abs(want), 1e-3 * absmean)
 
 
-REL_ABS = {pkg.MCMP2_MIXED: (2e-3, 1e-4), pkg.MCMP2_TF32: (6.4e-2, 3.2e-3)}
-C_SUM = {pkg.MCMP2_GAUNT: 6.25, pkg.MCMP2_BREIT: 9.0}
+FORMS = {pkg.MCMP2_MIXED: bounds.BF16X3, pkg.MCMP2_TF32: bounds.TF32}
 
 
-def _tol(prec, interaction, want, abs_sum):
-    rel, ab = REL_ABS[prec]
-    return rel * np.abs(want) + ab * C_SUM[interaction] * abs_sum
+def _steps_tol(orc, r, tau, prec, interaction):
+    """Tolerance of each replayed step estimate: the error model of the form with the operators."""
+    return bounds.steps_tolerance(orc, r, tau, FORMS[prec], interaction)
 
 
 @pytest.mark.parametrize("interaction", [pkg.MCMP2_GAUNT, pkg.MCMP2_BREIT])
@@ -108,8 +100,8 @@ def test_interaction_tensor_forms_match_oracle(tiny, strong, prec, interaction, 
     ctx = pkg.Context(system, m, n_tau, prec)
     ctx.set_interaction(interaction)
     got = ctx.eval_fixed(r, tau)
-    want, abs_sum = orc.eval_steps(r, tau, with_abs=True)
-    tol = _tol(prec, interaction, want, abs_sum)
+    want = orc.eval_steps(r, tau)
+    tol = _steps_tol(orc, r, tau, prec, interaction)
     assert np.all(np.abs(got - want) <= tol), (got, want, tol)
     if which == "strong" and m > 2 and prec == pkg.MCMP2_MIXED:
         # the operator terms move the estimate by far more than the split BF16 tolerance
@@ -128,8 +120,8 @@ def test_breit_tensor_forms_medium_system(prec):
     ctx = pkg.Context(medium, m, n_tau, prec)
     ctx.set_interaction(pkg.MCMP2_BREIT)
     got = ctx.eval_fixed(r, tau)
-    want, abs_sum = orc.eval_steps(r, tau, with_abs=True)
-    assert np.all(np.abs(got - want) <= _tol(prec, pkg.MCMP2_BREIT, want, abs_sum)), (got, want)
+    want = orc.eval_steps(r, tau)
+    assert np.all(np.abs(got - want) <= _steps_tol(orc, r, tau, prec, pkg.MCMP2_BREIT)), (got, want)
 
 
 @pytest.mark.parametrize("prec,interaction", [(pkg.MCMP2_MIXED, pkg.MCMP2_BREIT), (pkg.MCMP2_MIXED, pkg.MCMP2_GAUNT),
@@ -156,7 +148,7 @@ def test_interaction_full_size_sampled_tiles(prec, interaction):
         vals = orc.eval_pairs(r[0], tau[0], ps, qs)
         want = vals.sum(axis=0)
         k = sum(nb - b for b in range(bp)) + (bq - bp)
-        tol = _tol(prec, interaction, want, np.abs(vals).sum(axis=0))
+        tol = bounds.tile_tolerance(orc, r[0], tau[0], pairs, FORMS[prec], interaction)
         assert np.all(np.abs(partials[:, k] - want) <= tol), (bp, bq, partials[:, k], want, tol)
 
 

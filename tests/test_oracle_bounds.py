@@ -79,3 +79,32 @@ def test_model_terms_add_for_the_forms(strong):
     s = {f: bounds.element_model(orc, r, tau, pairs, form)[1] for f, form in
          (("fp64", bounds.FP64), ("bf16", bounds.BF16X3), ("tf32", bounds.TF32))}
     assert np.all(s["fp64"] < 1e-6 * s["bf16"]) and np.all(s["bf16"] < s["tf32"])
+
+
+def test_sum_model_sigma_matches_a_perturbation_experiment(strong):
+    """The standard deviation of a SUM of summands that share walker pairs: perturbing each
+    position's operands once (shared by all its summands) moves the sum as sum_model says;
+    adding the per-summand sigmas in quadrature would miss the correlation."""
+    import torch
+
+    orc = oracle.Oracle(strong, interaction=2)
+    m = 10
+    r = synthetic.walker_positions(strong.centres, 1, m, seed=83)[0]
+    tau = synthetic.imaginary_times(orc.lam(), 1, 1, seed=84)[0]
+    pairs = [(p, q) for p in range(m) for q in range(p + 1, m)]
+    s = 1e-7
+    form = bounds.Form(u_gemm=0.0, u_rep=s, u_acc=0.0, u_pack=0.0, u_epi=0.0)
+    sig, _ = bounds.sum_model(orc, r, tau, pairs, form, 2)
+    ts = bounds.TileSetup(orc, r, pairs, 2)
+    XU = ts.PHU * ts.scales(tau[0])[None, None, :, None]
+    rng = np.random.default_rng(6)
+    with torch.no_grad():
+        base = float(bounds.summands(ts, torch.tensor(np.stack([XU[ts.ip, 0], XU[ts.ip, 1], XU[ts.iq, 0],
+                                                                XU[ts.iq, 1]])))[0].sum())
+        draws = []
+        for _ in range(400):
+            Y = XU + s * np.abs(XU) * (rng.standard_normal(XU.shape) + 1j * rng.standard_normal(XU.shape))
+            X = np.stack([Y[ts.ip, 0], Y[ts.ip, 1], Y[ts.iq, 0], Y[ts.iq, 1]])
+            draws.append(float(bounds.summands(ts, torch.tensor(X))[0].sum()) - base)
+    ratio = np.std(draws) / sig[0]
+    assert 0.85 < ratio < 1.15, ratio
