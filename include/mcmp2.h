@@ -89,7 +89,7 @@ typedef struct mcmp2_ctx mcmp2_ctx;
 
 /* Problem sizes that fix the workspace. */
 typedef struct {
-    int n_centres;    /* atoms (centres of basis shells and of g) */
+    int n_centres;    /* atoms (centres of basis shells and of g), 1 .. 256 */
     int n_functions;  /* n_L, scalar Cartesian Gaussians after shell expansion */
     int n_occ;        /* occupied positive-energy spinors (even, >= 2) */
     int n_vir;        /* virtual positive-energy spinors (even, >= 2) */

@@ -168,5 +168,6 @@ __host__ __device__ inline long long n_tiles_for(int m, int tile_pairs)
 // of 8 pairs, so every tile count and grid dimension fits an int.
 constexpr int MAX_WALKER_PAIRS = 1 << 16;
 constexpr int MAX_TAU = 64;  // imaginary times per step
+constexpr int MAX_CENTRES = 256;  // atoms (the Metropolis kernel stages 4 x 4 x n_centres doubles per block)
 
 }  // namespace mcmp2

@@ -9,66 +9,100 @@ namespace mcmp2 {
 // displacement in [-delta, delta]^3; the move is accepted with probability
 // min(1, w'/w) with w = g(r1) g(r2) / r12 (the 1/N_g cancels).  FP64 with
 // explicit rounding so the same counters give the same walk on the host.
-// Four lanes share a pair: lane j evaluates g for electron j&1 at the old (j<2)
-// or proposed (j>=2) position (g is FP64-exp bound on GB300).  The pair's
-// weight factor a_p = N_g / (g(r1) g(r2)) at the resulting positions is
-// written as well (a may be null).
-__global__ void metropolis_kernel(DevSystem s, double *__restrict__ r,
-                                  const unsigned long long *__restrict__ step_ptr, uint64_t seed,
-                                  double delta, unsigned long long *__restrict__ accepted, double *__restrict__ a)
+// g is FP64-exp bound on GB300, so its terms are spread over the block: one
+// thread per (pair, position, centre) evaluates that centre's two Gaussians at
+// one of the pair's four positions (old and proposed r1, r2), and one thread per
+// pair then adds the centres in order (the rounding of weight_g) and decides the
+// move.  The pair's weight factor a_p = N_g / (g(r1) g(r2)) at the resulting
+// positions is written as well (a may be null).
+constexpr int MET_PAIRS = 4;     // walker pairs per block
+constexpr int MET_THREADS = 128;
+
+__device__ __forceinline__ double centre_term(const DevSystem &s, int i, double x, double y, double z)
 {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = gid >> 2, j = gid & 3;
-    const bool live = p < s.m;
-    const int lane = threadIdx.x & 31, g0 = lane & ~3;
-    double pos[3] = {0.0, 0.0, 0.0};
-    double o1[3] = {0.0, 0.0, 0.0}, o2[3] = {0.0, 0.0, 0.0}, n1[3] = {0.0, 0.0, 0.0}, n2[3] = {0.0, 0.0, 0.0};
-    uint32_t u_acc = 0;
-    if (live) {
-        const uint64_t step = *step_ptr;
-        const uint4 A = draw4(seed, step, (uint32_t)p, 0u);
-        const uint4 B = draw4(seed, step, (uint32_t)p, 1u);
-        const uint32_t u[7] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z};
-        const double *r1 = r + 6 * p, *r2 = r1 + 3;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            o1[k] = r1[k];
-            o2[k] = r2[k];
-            n1[k] = __dadd_rn(o1[k], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[k])), 1.0)));
-            n2[k] = __dadd_rn(o2[k], __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[3 + k])), 1.0)));
-        }
-        u_acc = u[6];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) pos[k] = (j == 0) ? o1[k] : (j == 1) ? o2[k] : (j == 2) ? n1[k] : n2[k];
-    }
-    const double gj = live ? weight_g(s, pos[0], pos[1], pos[2]) : 1.0;
-    const double g1o = __shfl_sync(0xffffffffu, gj, g0 + 0), g2o = __shfl_sync(0xffffffffu, gj, g0 + 1);
-    const double g1n = __shfl_sync(0xffffffffu, gj, g0 + 2), g2n = __shfl_sync(0xffffffffu, gj, g0 + 3);
-    unsigned int acc = 0;
-    if (live && j == 0) {
-        auto r12 = [](const double *x1, const double *x2) {
-            const double dx = __dsub_rn(x1[0], x2[0]), dy = __dsub_rn(x1[1], x2[1]), dz = __dsub_rn(x1[2], x2[2]);
-            return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-        };
-        const double w_old = __ddiv_rn(__dmul_rn(g1o, g2o), r12(o1, o2));
-        const double w_new = __ddiv_rn(__dmul_rn(g1n, g2n), r12(n1, n2));
-        double *r1 = r + 6 * p, *r2 = r1 + 3;
-        double ga = g1o, gb = g2o;
-        if (__dmul_rn(u32_open(u_acc), w_old) < w_new) {
+    const double dx = __dsub_rn(x, s.centres[3 * i + 0]);
+    const double dy = __dsub_rn(y, s.centres[3 * i + 1]);
+    const double dz = __dsub_rn(z, s.centres[3 * i + 2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double *w = s.wcoef + 4 * i;
+    const double t1 = __dmul_rn(w[0], exp(__dmul_rn(-w[1], d2)));
+    const double t2 = __dmul_rn(w[2], exp(__dmul_rn(-w[3], d2)));
+    return __dadd_rn(t1, t2);
+}
+
+__global__ void __launch_bounds__(MET_THREADS) metropolis_kernel(DevSystem s, double *__restrict__ r,
+                                                                 const unsigned long long *__restrict__ step_ptr,
+                                                                 uint64_t seed, double delta,
+                                                                 unsigned long long *__restrict__ accepted,
+                                                                 double *__restrict__ a)
+{
+    extern __shared__ double terms[];          // [MET_PAIRS][4][n_centres]
+    __shared__ double spos[MET_PAIRS][4][3];   // old r1, old r2, proposed r1, proposed r2
+    __shared__ uint32_t su[MET_PAIRS];         // the acceptance draw
+    __shared__ unsigned int sacc;
+    const int nc = s.n_centres;
+    const int p0 = blockIdx.x * MET_PAIRS;
+    if (threadIdx.x == 0) sacc = 0;
+    if (threadIdx.x < MET_PAIRS) {
+        const int lp = threadIdx.x, p = p0 + lp;
+        if (p < s.m) {
+            const uint64_t step = *step_ptr;
+            const uint4 A = draw4(seed, step, (uint32_t)p, 0u);
+            const uint4 B = draw4(seed, step, (uint32_t)p, 1u);
+            const uint32_t u[7] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z};
+            const double *r1 = r + 6 * p, *r2 = r1 + 3;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                r1[k] = n1[k];
-                r2[k] = n2[k];
+                const double o1 = r1[k], o2 = r2[k];
+                spos[lp][0][k] = o1;
+                spos[lp][1][k] = o2;
+                spos[lp][2][k] = __dadd_rn(o1, __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[k])), 1.0)));
+                spos[lp][3][k] = __dadd_rn(o2, __dmul_rn(delta, __dsub_rn(__dmul_rn(2.0, u32_open(u[3 + k])), 1.0)));
             }
-            ga = g1n;
-            gb = g2n;
-            acc = 1;
+            su[lp] = u[6];
         }
-        if (a) a[p] = s.Ng / (ga * gb);
     }
-    // One atomic per warp.
-    const unsigned int total = __reduce_add_sync(0xffffffffu, acc);
-    if (lane == 0 && total) atomicAdd(accepted, (unsigned long long)total);
+    __syncthreads();
+    const int per_pair = 4 * nc;
+    for (int w = threadIdx.x; w < MET_PAIRS * per_pair; w += MET_THREADS) {
+        const int lp = w / per_pair, rem = w - lp * per_pair;
+        const int j = rem / nc, i = rem - j * nc;
+        if (p0 + lp < s.m) terms[w] = centre_term(s, i, spos[lp][j][0], spos[lp][j][1], spos[lp][j][2]);
+    }
+    __syncthreads();
+    if (threadIdx.x < MET_PAIRS) {
+        const int lp = threadIdx.x, p = p0 + lp;
+        if (p < s.m) {
+            double g[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {  // centres added in order, as weight_g does
+                double v = 0.0;
+                for (int i = 0; i < nc; ++i) v = __dadd_rn(v, terms[lp * per_pair + j * nc + i]);
+                g[j] = v;
+            }
+            auto r12 = [](const double *x1, const double *x2) {
+                const double dx = __dsub_rn(x1[0], x2[0]), dy = __dsub_rn(x1[1], x2[1]), dz = __dsub_rn(x1[2], x2[2]);
+                return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+            };
+            const double w_old = __ddiv_rn(__dmul_rn(g[0], g[1]), r12(spos[lp][0], spos[lp][1]));
+            const double w_new = __ddiv_rn(__dmul_rn(g[2], g[3]), r12(spos[lp][2], spos[lp][3]));
+            double ga = g[0], gb = g[1];
+            if (__dmul_rn(u32_open(su[lp]), w_old) < w_new) {
+                double *r1 = r + 6 * p, *r2 = r1 + 3;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    r1[k] = spos[lp][2][k];
+                    r2[k] = spos[lp][3][k];
+                }
+                ga = g[2];
+                gb = g[3];
+                atomicAdd(&sacc, 1u);
+            }
+            if (a) a[p] = s.Ng / (ga * gb);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sacc) atomicAdd(accepted, (unsigned long long)sacc);  // one atomic per block
 }
 
 // a_p = N_g / (g(r1p) g(r2p)): with 1/(w w) this is the weight factor of a pair of pairs.
@@ -89,11 +123,16 @@ __global__ void pair_weights_kernel(DevSystem s, const double *__restrict__ r, d
 // product X X^dagger of scaled spinor values carries exp(+eps_i tau) or
 // exp(-eps_a tau) times exp(-eps_HOMO tau) or exp(+eps_LUMO tau); every factor
 // is at most 1 and the four shifts of a pair of pairs multiply to exp(lambda tau).
-__global__ void times_kernel(DevSystem s, const unsigned long long *__restrict__ step_ptr, uint64_t seed,
-                             const double *__restrict__ tau_given, double *__restrict__ tau,
-                             double *__restrict__ scale, float *__restrict__ scale_f)
+// Block (c, t) handles orbitals 128 c .. 128 c + 127 of time t (each block draws
+// the time itself; FP64 exp is slow on GB300, so the orbitals are spread wide).
+constexpr int TIMES_THREADS = 128;
+__global__ void __launch_bounds__(TIMES_THREADS) times_kernel(DevSystem s,
+                                                              const unsigned long long *__restrict__ step_ptr,
+                                                              uint64_t seed, const double *__restrict__ tau_given,
+                                                              double *__restrict__ tau, double *__restrict__ scale,
+                                                              float *__restrict__ scale_f)
 {
-    const int t = blockIdx.x;
+    const int t = blockIdx.y;
     __shared__ double tt;
     if (threadIdx.x == 0) {
         double v;
@@ -104,11 +143,11 @@ __global__ void times_kernel(DevSystem s, const unsigned long long *__restrict__
             v = -log(u53_half_open(o.x, o.y)) / s.lambda;
         }
         tt = v;
-        tau[t] = v;
+        if (blockIdx.x == 0) tau[t] = v;
     }
     __syncthreads();
     const double x = tt;
-    for (int k = threadIdx.x; k < s.n_orb; k += blockDim.x) {
+    for (int k = blockIdx.x * TIMES_THREADS + threadIdx.x; k < s.n_orb; k += gridDim.x * TIMES_THREADS) {
         const double e = s.eps[k];
         const double arg = (k < s.n_occ) ? (e - s.eps_homo) : -(e - s.eps_lumo);
         const double v = exp(0.5 * arg * x);
@@ -164,9 +203,9 @@ cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long
                               uint64_t seed, double delta, unsigned long long *accepted, double *a,
                               cudaStream_t st)
 {
-    const int threads = 64;  // FP64 exp-bound: spread the 4 m lanes over as many SMs as possible
-    const int lanes = 4 * s.m;
-    metropolis_kernel<<<(lanes + threads - 1) / threads, threads, 0, st>>>(s, r, step, seed, delta, accepted, a);
+    const size_t smem = sizeof(double) * MET_PAIRS * 4 * s.n_centres;  // 256 centres fit the default 48 KB
+    metropolis_kernel<<<(s.m + MET_PAIRS - 1) / MET_PAIRS, MET_THREADS, smem, st>>>(s, r, step, seed, delta,
+                                                                                    accepted, a);
     return cudaGetLastError();
 }
 
@@ -180,7 +219,8 @@ cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, 
 cudaError_t launch_times(const DevSystem &s, const unsigned long long *step, uint64_t seed,
                          const double *tau_given, double *tau, double *scale, float *scale_f, cudaStream_t st)
 {
-    times_kernel<<<s.n_tau, 256, 0, st>>>(s, step, seed, tau_given, tau, scale, scale_f);
+    const dim3 grid((s.n_orb + TIMES_THREADS - 1) / TIMES_THREADS, s.n_tau);
+    times_kernel<<<grid, TIMES_THREADS, 0, st>>>(s, step, seed, tau_given, tau, scale, scale_f);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ struct Layout {
 
 bool dims_valid(const mcmp2_dims *d)
 {
-    return d && d->n_centres >= 1 && d->n_functions >= 1 && d->n_occ >= 2 && d->n_vir >= 2 && d->m >= 2 &&
+    return d && d->n_centres >= 1 && d->n_centres <= MAX_CENTRES && d->n_functions >= 1 && d->n_occ >= 2 && d->n_vir >= 2 && d->m >= 2 &&
            d->n_tau >= 1 && d->n_occ % 2 == 0 && d->n_vir % 2 == 0 && d->n_functions <= 65536 &&
            d->m <= MAX_WALKER_PAIRS && d->n_tau <= MAX_TAU && d->n_occ + d->n_vir <= 65536;
 }
