@@ -146,6 +146,8 @@ struct mcmp2_ctx {
     double graph_pair_ms = 0.0;
     // CUDA graph of one production step (replayed by run_steps)
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;           // the captured step's branch for the imaginary times
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_seed = 0;
     double graph_delta = 0.0;
@@ -232,6 +234,9 @@ void mcmp2_destroy(mcmp2_ctx *ctx)
     drop_events(ctx);
     ctx->drop_graph();
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     for (auto &e : ctx->gev)
         if (e) cudaEventDestroy(e);
     mixed_release(ctx->mixed);
@@ -511,7 +516,7 @@ int reset_stats(mcmp2_ctx *ctx)
 // given) to I'_n in out_slot.  Optionally updates statistics and advances the step.
 int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uint64_t seed, double *out_slot,
                    int update, bool advance, bool weights_ready = false, cudaStream_t st_in = nullptr,
-                   cudaEvent_t *fixed_ev = nullptr, const DebugTile &dbg = DebugTile{})
+                   cudaEvent_t *fixed_ev = nullptr, const DebugTile &dbg = DebugTile{}, bool times_ready = false)
 {
     const Layout &L = ctx->L;
     const DevSystem &S = ctx->sys;
@@ -526,8 +531,10 @@ int step_integrand(mcmp2_ctx *ctx, const double *r, const double *tau_given, uin
         ctx->launches += 1;
     }
     float *scale_f = ctx->precision != MCMP2_FP64 ? ctx->at<float>(L.scale_f) : nullptr;
-    CK(launch_times(S, step, seed, tau_given, tau, scale, scale_f, st), "imaginary times");
-    ctx->launches += 1;
+    if (!times_ready) {
+        CK(launch_times(S, step, seed, tau_given, tau, scale, scale_f, st), "imaginary times");
+        ctx->launches += 1;
+    }
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (fixed_ev) {
         ev[0] = fixed_ev[0];
@@ -647,19 +654,35 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
                   ctx->graph_timing != ctx->timing)) {
         ctx->drop_graph();
         if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
+        if (!ctx->side_stream) CK(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking), "side stream");
+        if (!ctx->fork_ev) CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "event");
+        if (!ctx->join_ev) CK(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming), "event");
         if (ctx->timing && !ctx->gev[0]) {
             CK(cudaEventCreate(&ctx->gev[0]), "event");
             CK(cudaEventCreate(&ctx->gev[1]), "event");
         }
         const long long l0 = ctx->launches, p0 = ctx->pair_launches;
         CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        int rc = ctx->cuda(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta,
+        // The imaginary times depend only on the step counter: a side branch
+        // draws them while the Metropolis move runs.
+        int rc = ctx->cuda(cudaEventRecord(ctx->fork_ev, ctx->cap_stream), "fork");
+        if (rc == MCMP2_OK) rc = ctx->cuda(cudaStreamWaitEvent(ctx->side_stream, ctx->fork_ev, 0), "fork");
+        if (rc == MCMP2_OK)
+            rc = ctx->cuda(launch_times(ctx->sys, ctx->at<unsigned long long>(L.step), seed, nullptr,
+                                        ctx->at<double>(L.tau), ctx->at<double>(L.scale),
+                                        ctx->precision != MCMP2_FP64 ? ctx->at<float>(L.scale_f) : nullptr,
+                                        ctx->side_stream),
+                           "imaginary times");
+        if (rc == MCMP2_OK) rc = ctx->cuda(cudaEventRecord(ctx->join_ev, ctx->side_stream), "join");
+        if (rc == MCMP2_OK)
+            rc = ctx->cuda(launch_metropolis(ctx->sys, r, ctx->at<unsigned long long>(L.step), seed, ctx->delta,
                                              &stats->accepted, ctx->at<double>(L.a), ctx->cap_stream),
                            "metropolis");
-        ctx->launches += 1;
+        if (rc == MCMP2_OK) rc = ctx->cuda(cudaStreamWaitEvent(ctx->cap_stream, ctx->join_ev, 0), "join");
+        ctx->launches += 2;
         if (rc == MCMP2_OK)
             rc = step_integrand(ctx, r, nullptr, seed, ctx->at<double>(L.per_step), 1, true, true, ctx->cap_stream,
-                                ctx->timing ? ctx->gev : nullptr);
+                                ctx->timing ? ctx->gev : nullptr, DebugTile{}, true);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
         ctx->graph_launches = ctx->launches - l0;
