@@ -108,11 +108,19 @@ __global__ void basis_split_kernel(DevSystem s, const double *__restrict__ r, __
 // ===========================================================================
 // 2. Spinor formation with fused scale-and-split epilogue
 // ===========================================================================
+// Runs on CTA pairs (clusters of two CTAs on the two SMs of a TPC).  A work
+// unit is (position block pair MT, component pair cp, 64-orbital block kb):
+// CTA r owns the 128 positions of block 2 MT + r as its half of the A operand
+// of an M = 256 MMA and holds the coefficient rows of component 2 cp + r (64
+// orbitals, re and im) as its half of the N = 256 B operand, so each CTA's
+// tensor memory collects [re | im] of both components for its own positions,
+// and each operand tile read from L2 serves twice the work of a one-CTA
+// 128 x 128 tile.
 constexpr int SP_STAGES = 4;
-constexpr int SP_STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo
-constexpr int SP_EPI_WARPS = 8;                 // two per tensor-memory lane quarter, one per half tile
-constexpr int SP_THREADS = 64 + 32 * SP_EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
-constexpr int SP_TMEM_COLS = 256;               // two 128-column accumulators
+constexpr int SP_STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo (this CTA's halves)
+constexpr int SP_EPI_WARPS = 8;                 // two per tensor-memory lane quarter, one per half of 64 orbitals
+constexpr int SP_THREADS = 64 + 32 * SP_EPI_WARPS;  // TMA warp, MMA (even CTA) or relay (odd CTA) warp, epilogue warps
+constexpr int SP_TMEM_COLS = 512;               // two 256-column accumulators: 2 components x [re | im]
 constexpr int SP_MAX_TAU = 64;                  // scale staging capacity (the API limits n_tau to 64)
 constexpr int SP_BOX_BYTES = 32 * 128;          // one TMA store box: 32 rows x one 128-byte chunk
 constexpr int SP_WARP_STAGE = 2 * SP_BOX_BYTES;  // X and iX boxes of one epilogue warp
@@ -137,23 +145,21 @@ struct SpinorArgs {
     int ncomp; // spinor components: 4, or 2 (two-component systems: large components only, rows 2x + c)
 };
 
-// Tile slot of CTA b on its j-th tile: rounds of G = gridDim.x slots, every
-// other round in reverse CTA order.  Slots list the small-component tiles
-// (K = 3 n_L) before the large-component ones (K = n_L), so the snake order
-// gives every CTA a near-equal number of K chunks (78 against 97 for a plain
-// stride at the medium size).
+// Unit slot of cluster b on its j-th unit: rounds of G = number of clusters,
+// every other round in reverse cluster order.  Slots list the units of the
+// small components (K = 3 n_L) before those of the large ones (K = n_L), so
+// the snake order gives every cluster a near-equal number of K chunks (39
+// against an average of 36.9 at the medium size).
 __device__ __forceinline__ int sp_slot(int j, int b, int G) { return j * G + ((j & 1) ? G - 1 - b : b); }
 
-__device__ __forceinline__ void sp_tile(int slot, int n_mt, int n_kb, int ncomp, int &mt, int &c4, int &kb)
+__device__ __forceinline__ void sp_unit(int slot, int n_MT, int n_kb, int ncomp, int &MT, int &cp, int &kb)
 {
-    const int n_small = ncomp == 4 ? n_mt * 2 * n_kb : 0;  // tiles of components 2, 3
-    const bool small = slot < n_small;
-    const int u = small ? slot : slot - n_small;
-    mt = u / (2 * n_kb);
-    const int r = u - mt * 2 * n_kb;
-    const int half = r / n_kb;
-    c4 = (small ? 2 : 0) + half;
-    kb = r - half * n_kb;
+    const int n_heavy = ncomp == 4 ? n_MT * n_kb : 0;  // units of components 2, 3
+    const bool heavy = slot < n_heavy;
+    const int u = heavy ? slot : slot - n_heavy;
+    MT = u / n_kb;
+    kb = u - MT * n_kb;
+    cp = heavy ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __grid_constant__ SpinorMaps maps,
@@ -164,30 +170,36 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + SP_BARS_OFF);
     uint64_t *empty = full + SP_STAGES;
-    uint64_t *tfull = empty + SP_STAGES;  // [2]
-    uint64_t *tempty = tfull + 2;         // [2]
+    uint64_t *tfull = empty + SP_STAGES;  // [2] accumulator complete (both CTAs, multicast)
+    uint64_t *tempty = tfull + 2;         // [2] accumulator read out (even CTA: both CTAs' epilogue warps)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = args.n_mt * args.ncomp * args.n_kb;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int cid = (int)cluster_id(), ncl = (int)cluster_count();
+    const int n_MT = (args.n_mt + 1) / 2;
+    const int n_units = n_MT * (args.ncomp / 2) * args.n_kb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < SP_STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], leader ? 2 : 1);  // even CTA: its own copies + the odd CTA's relay
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], SP_EPI_WARPS);
+            mbar_init(&tempty[b], 2 * SP_EPI_WARPS);
         }
         mbar_init_fence();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, SP_TMEM_COLS);
+    if (warp == 1) tmem_alloc_pair(tmem_slot, SP_TMEM_COLS);
     fence_before();
     __syncthreads();
+    cluster_sync();  // barriers of both CTAs initialised before any remote arrive or multicast commit
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
         if (lane == 0) {
             for (int i = 0; i < 8; ++i) tma_prefetch(&maps.m[i]);
             int stage = 0;
@@ -195,13 +207,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             int issued[SP_STAGES] = {};
             uint32_t issued_phase[SP_STAGES] = {};
             bool ok = true;
-            for (int jt = 0, tile; ok && (tile = sp_slot(jt, blockIdx.x, gridDim.x)) < n_tiles; ++jt) {
-                int mt, c4, kb;
-                sp_tile(tile, args.n_mt, args.n_kb, args.ncomp, mt, c4, kb);
-                const bool grad = c4 >= 2;
-                const CUtensorMap *mp = &maps.m[grad ? 4 : 0];
-                const int K = grad ? 3 * args.nl : args.nl;
-                const int wt_row = ((c4 & 1) * args.n_kb + kb) * 128;
+            for (int jt = 0, slot; ok && (slot = sp_slot(jt, cid, ncl)) < n_units; ++jt) {
+                int MT, cp, kb;
+                sp_unit(slot, n_MT, args.n_kb, args.ncomp, MT, cp, kb);
+                const CUtensorMap *mp = &maps.m[cp ? 4 : 0];
+                const int K = cp ? 3 * args.nl : args.nl;
+                const int a_row = (2 * MT + (int)rank) * 128;  // past the last block: zero fill, never stored
+                const int wt_row = ((int)rank * args.n_kb + kb) * 128;  // component 2 cp + rank
                 for (int c = 0; c < n_chunks(K); ++c) {
                     if (!mbar_wait_fast(&empty[stage], phase ^ 1u, args.abort_flag, 11, TIMEOUT_NS)) {
                         ok = false;
@@ -209,8 +221,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                     }
                     unsigned char *st = smem + stage * SP_STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[stage], SP_STAGE_BYTES);
-                    tma_load_2d(st + 0 * TILE_BYTES, mp + 0, &full[stage], c * BK, mt * 128);
-                    tma_load_2d(st + 1 * TILE_BYTES, mp + 1, &full[stage], c * BK, mt * 128);
+                    tma_load_2d(st + 0 * TILE_BYTES, mp + 0, &full[stage], c * BK, a_row);
+                    tma_load_2d(st + 1 * TILE_BYTES, mp + 1, &full[stage], c * BK, a_row);
                     tma_load_2d(st + 2 * TILE_BYTES, mp + 2, &full[stage], c * BK, wt_row);
                     tma_load_2d(st + 3 * TILE_BYTES, mp + 3, &full[stage], c * BK, wt_row);
                     issued[stage] = 1;
@@ -225,26 +237,51 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                 for (int s = 0; s < SP_STAGES; ++s)
                     if (issued[s]) mbar_drain(&full[s], issued_phase[s], TIMEOUT_NS);
         }
+    } else if (warp == 1 && !leader) {
+        // ---------------- relay (odd CTA): its copies landed -> the even CTA's stage barrier ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int jt = 0, slot; ok && (slot = sp_slot(jt, cid, ncl)) < n_units; ++jt) {
+                int MT, cp, kb;
+                sp_unit(slot, n_MT, args.n_kb, args.ncomp, MT, cp, kb);
+                const int K = cp ? 3 * args.nl : args.nl;
+                for (int c = 0; c < n_chunks(K); ++c) {
+                    if (!mbar_wait(&full[stage], phase, args.abort_flag, 15, TIMEOUT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_shared(&full[stage], 0));
+                    if (++stage == SP_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
     } else if (warp == 1) {
+        // ---------------- MMA issuer (even CTA) ----------------
         if (lane == 0) {
             int stage = 0, buf = 0;
             uint32_t phase = 0, tphase[2] = {0, 0};
             bool ok = true;
-            const uint32_t id = idesc_bf16(128, false);
+            const uint32_t id = idesc_pair(idesc_bf16(256, false));
+            constexpr uint16_t BOTH = 3;
             // Stage-0 descriptors; a stage or K step adds its byte offset / 16 to the address field.
             const uint32_t base0 = smem_u32(smem);
             const uint64_t ah0 = sdesc_sw64(base0 + 0 * TILE_BYTES), al0 = sdesc_sw64(base0 + 1 * TILE_BYTES);
             const uint64_t bh0 = sdesc_sw64(base0 + 2 * TILE_BYTES), bl0 = sdesc_sw64(base0 + 3 * TILE_BYTES);
-            for (int jt = 0, tile; ok && (tile = sp_slot(jt, blockIdx.x, gridDim.x)) < n_tiles; ++jt) {
-                int mt, c4, kb;
-                sp_tile(tile, args.n_mt, args.n_kb, args.ncomp, mt, c4, kb);
-                const int K = c4 >= 2 ? 3 * args.nl : args.nl;
+            for (int jt = 0, slot; ok && (slot = sp_slot(jt, cid, ncl)) < n_units; ++jt) {
+                int MT, cp, kb;
+                sp_unit(slot, n_MT, args.n_kb, args.ncomp, MT, cp, kb);
+                const int K = cp ? 3 * args.nl : args.nl;
                 if (!mbar_wait_fast(&tempty[buf], tphase[buf] ^ 1u, args.abort_flag, 12, TIMEOUT_NS)) {
                     ok = false;
                     break;
                 }
                 fence_after();
-                const uint32_t d = tmem + 128u * buf;
+                const uint32_t d = tmem + 256u * buf;
                 for (int c = 0; c < n_chunks(K); ++c) {
                     if (!mbar_wait_fast(&full[stage], phase, args.abort_flag, 13, TIMEOUT_NS)) {
                         ok = false;
@@ -256,31 +293,32 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                     for (int ks = 0; ks < ksteps; ++ks) {
                         const uint64_t so = (uint64_t)((stage * SP_STAGE_BYTES + ks * 32) >> 4);
                         const uint64_t ah = ah0 + so, al = al0 + so, bh = bh0 + so, bl = bl0 + so;
-                        umma(d, ah, bh, id, (c == 0 && ks == 0) ? 0u : 1u);
-                        umma(d, ah, bl, id, 1u);
-                        umma(d, al, bh, id, 1u);
+                        umma_pair(d, ah, bh, id, (c == 0 && ks == 0) ? 0u : 1u);
+                        umma_pair(d, ah, bl, id, 1u);
+                        umma_pair(d, al, bh, id, 1u);
                     }
-                    umma_commit(&empty[stage]);
+                    umma_pair_commit(&empty[stage], BOTH);
                     if (++stage == SP_STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
                 }
                 if (!ok) break;
-                umma_commit(&tfull[buf]);
+                umma_pair_commit(&tfull[buf], BOTH);
                 tphase[buf] ^= 1u;
                 buf ^= 1;
             }
             // Let every MMA this thread issued finish before tensor memory is freed.
-            umma_commit(&empty[stage]);
+            umma_pair_commit(&empty[stage], 1);
             mbar_drain(&empty[stage], phase, TIMEOUT_NS);
         }
     } else {
-        // Epilogue: each lane owns one position row of the tile; the two warps of a
-        // lane quarter take orbitals 0-31 and 32-63 (chunks 2 jh, 2 jh + 1) of the
-        // 64-orbital block.  A warp reads its accumulator columns (re and im of its 32
-        // orbitals for its 32 rows) from tensor memory once per tile and releases the
-        // buffer at once.  Then, for every time and chunk, it stages its 32 rows of the
+        // Epilogue: each lane owns one position row of its CTA's 128; the two warps of
+        // a lane quarter take orbitals 0-31 and 32-63 (chunks 2 jh, 2 jh + 1) of the
+        // 64-orbital block, for both components of the unit in turn.  A warp reads a
+        // component's accumulator columns (re and im of its 32 orbitals for its 32
+        // rows) from tensor memory, and releases the buffer once it holds the second
+        // component's.  Then, for every time and chunk, it stages its 32 rows of the
         // chunk in shared memory in the contraction's operand order (re_hi, re_lo,
         // im_hi, im_lo, 32 B each; or re, im as TF32, 64 B each; 128-byte swizzle), and
         // the same rows of iX = i X (halves swapped, the new first half negated), and
@@ -296,23 +334,14 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         const int sw = lane & 7;                                       // 128-byte swizzle of this lane's row
         int buf = 0;
         uint32_t ephase[2] = {0, 0};
-        for (int jt = 0, tile; (tile = sp_slot(jt, blockIdx.x, gridDim.x)) < n_tiles; ++jt) {
-            int mt, c4, kb;
-            sp_tile(tile, args.n_mt, args.n_kb, args.ncomp, mt, c4, kb);
+        for (int jt = 0, slot; (slot = sp_slot(jt, cid, ncl)) < n_units; ++jt) {
+            int MT, cp, kb;
+            sp_unit(slot, n_MT, args.n_kb, args.ncomp, MT, cp, kb);
+            const int mt = 2 * MT + (int)rank;
             const bool got = mbar_wait(&tfull[buf], ephase[buf], args.abort_flag, 14, TIMEOUT_NS);
             if (bar_any<1, 32 * SP_EPI_WARPS>(!got)) break;  // also: every epilogue warp is done with the previous scales
             ephase[buf] ^= 1u;
             fence_after();
-            float re[2][16], im[2][16];
-            tmem_ld<16>(lane_addr + 128u * buf + 32u * jh, re[0]);
-            tmem_ld<16>(lane_addr + 128u * buf + 32u * jh + 16u, re[1]);
-            tmem_ld<16>(lane_addr + 128u * buf + 64u + 32u * jh, im[0]);
-            tmem_ld<16>(lane_addr + 128u * buf + 64u + 32u * jh + 16u, im[1]);
-            tmem_wait_ld();
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);  // the accumulator is in registers: MMAs may reuse it
-            buf ^= 1;
             const bool occ = kb < args.n_kb_occ;
             const int kl = occ ? kb : kb - args.n_kb_occ;
             const int k_first = (occ ? 0 : args.n_occ) + kl * 64;  // absolute index of the block's first orbital
@@ -325,85 +354,104 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             }
             bar_sync<1, 32 * SP_EPI_WARPS>();
 #pragma unroll 1
-            for (int t = 0; t < args.n_tau; ++t) {
-#pragma unroll
-                for (int jj = 0; jj < 2; ++jj) {
-                    const int j = 2 * jh + jj;
-                    // A chunk past the region's last orbital is never read by the contraction.
-                    if (k_first + 16 * j >= k_end) continue;
-                    const float *st_ = sscale + 64 * t + 16 * j;
-                    uint4 d[8];
-                    if (args.tf32) {
-                        uint32_t rt[16], it[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float sc = st_[i];
-                            rt[i] = to_tf32(re[jj][i] * sc);
-                            it[i] = to_tf32(im[jj][i] * sc);
-                        }
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            d[v] = make_uint4(rt[4 * v], rt[4 * v + 1], rt[4 * v + 2], rt[4 * v + 3]);
-                            d[4 + v] = make_uint4(it[4 * v], it[4 * v + 1], it[4 * v + 2], it[4 * v + 3]);
-                        }
-                    } else {
-                        uint32_t rh[8], rl[8], ih[8], il[8];
-#pragma unroll
-                        for (int i = 0; i < 16; i += 2) {
-                            const float s0 = st_[i], s1 = st_[i + 1];
-                            const float xr0 = re[jj][i] * s0, xr1 = re[jj][i + 1] * s1;
-                            const float xi0 = im[jj][i] * s0, xi1 = im[jj][i + 1] * s1;
-                            const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
-                            const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
-                            rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
-                            ih[i / 2] = *reinterpret_cast<const uint32_t *>(&hi);
-                            rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
-                            il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
-                        }
-                        d[0] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                        d[1] = make_uint4(rh[4], rh[5], rh[6], rh[7]);
-                        d[2] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                        d[3] = make_uint4(rl[4], rl[5], rl[6], rl[7]);
-                        d[4] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                        d[5] = make_uint4(ih[4], ih[5], ih[6], ih[7]);
-                        d[6] = make_uint4(il[0], il[1], il[2], il[3]);
-                        d[7] = make_uint4(il[4], il[5], il[6], il[7]);
-                    }
-                    // The previous boxes must have been read out before they are overwritten.
-                    if (lane == 0) bulk_wait_read_all();
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c4 = 2 * cp + cc;
+                const uint32_t col = 256u * buf + 128u * cc + 32u * jh;
+                float re[2][16], im[2][16];
+                tmem_ld<16>(lane_addr + col, re[0]);
+                tmem_ld<16>(lane_addr + col + 16u, re[1]);
+                tmem_ld<16>(lane_addr + col + 64u, im[0]);
+                tmem_ld<16>(lane_addr + col + 80u, im[1]);
+                tmem_wait_ld();
+                if (cc == 1) {
+                    // Both components are in registers: the MMAs may reuse the accumulator.
+                    fence_before();
                     __syncwarp();
+                    if (lane == 0) mbar_arrive_cluster(mapa_shared(&tempty[buf], 0));
+                }
+#pragma unroll 1
+                for (int t = 0; t < args.n_tau; ++t) {
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        const int u = (v ^ sw) << 4;  // 128-byte swizzle: 16-byte unit v of row `lane`
-                        uint4 w = d[v ^ 4];
-                        const uint32_t f = v < 4 ? neg : 0u;
-                        w.x ^= f;
-                        w.y ^= f;
-                        w.z ^= f;
-                        w.w ^= f;
-                        *reinterpret_cast<uint4 *>(sx + lane * 128 + u) = d[v];
-                        *reinterpret_cast<uint4 *>(si + lane * 128 + u) = w;
-                    }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    const int x0 = kl * 256 + 64 * j, y0 = mt * 128 + 32 * quarter;
-                    if (lane == 0 && y0 < args.P) {
-                        // Box {64 elements, 1 component, 32 positions, 1 time}; positions past P are clipped.
-                        tma_store_4d(mx, sx, x0, c4, y0, t);
-                        tma_store_4d(mi, si, x0, c4, y0, t);
-                        bulk_commit();
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int j = 2 * jh + jj;
+                        // A chunk past the region's last orbital is never read by the contraction.
+                        if (k_first + 16 * j >= k_end) continue;
+                        const float *st_ = sscale + 64 * t + 16 * j;
+                        uint4 d[8];
+                        if (args.tf32) {
+                            uint32_t rt[16], it[16];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const float sc = st_[i];
+                                rt[i] = to_tf32(re[jj][i] * sc);
+                                it[i] = to_tf32(im[jj][i] * sc);
+                            }
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                d[v] = make_uint4(rt[4 * v], rt[4 * v + 1], rt[4 * v + 2], rt[4 * v + 3]);
+                                d[4 + v] = make_uint4(it[4 * v], it[4 * v + 1], it[4 * v + 2], it[4 * v + 3]);
+                            }
+                        } else {
+                            uint32_t rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+                            for (int i = 0; i < 16; i += 2) {
+                                const float s0 = st_[i], s1 = st_[i + 1];
+                                const float xr0 = re[jj][i] * s0, xr1 = re[jj][i + 1] * s1;
+                                const float xi0 = im[jj][i] * s0, xi1 = im[jj][i + 1] * s1;
+                                const __nv_bfloat162 hr = __floats2bfloat162_rn(xr0, xr1);
+                                const __nv_bfloat162 hi = __floats2bfloat162_rn(xi0, xi1);
+                                rh[i / 2] = *reinterpret_cast<const uint32_t *>(&hr);
+                                ih[i / 2] = *reinterpret_cast<const uint32_t *>(&hi);
+                                rl[i / 2] = pack_bf16(xr0 - __low2float(hr), xr1 - __high2float(hr));
+                                il[i / 2] = pack_bf16(xi0 - __low2float(hi), xi1 - __high2float(hi));
+                            }
+                            d[0] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                            d[1] = make_uint4(rh[4], rh[5], rh[6], rh[7]);
+                            d[2] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                            d[3] = make_uint4(rl[4], rl[5], rl[6], rl[7]);
+                            d[4] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                            d[5] = make_uint4(ih[4], ih[5], ih[6], ih[7]);
+                            d[6] = make_uint4(il[0], il[1], il[2], il[3]);
+                            d[7] = make_uint4(il[4], il[5], il[6], il[7]);
+                        }
+                        // The previous boxes must have been read out before they are overwritten.
+                        if (lane == 0) bulk_wait_read_all();
+                        __syncwarp();
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) {
+                            const int u = (v ^ sw) << 4;  // 128-byte swizzle: 16-byte unit v of row `lane`
+                            uint4 w = d[v ^ 4];
+                            const uint32_t f = v < 4 ? neg : 0u;
+                            w.x ^= f;
+                            w.y ^= f;
+                            w.z ^= f;
+                            w.w ^= f;
+                            *reinterpret_cast<uint4 *>(sx + lane * 128 + u) = d[v];
+                            *reinterpret_cast<uint4 *>(si + lane * 128 + u) = w;
+                        }
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        const int x0 = kl * 256 + 64 * j, y0 = mt * 128 + 32 * quarter;
+                        if (lane == 0 && y0 < args.P) {
+                            // Box {64 elements, 1 component, 32 positions, 1 time}; positions past P are clipped.
+                            tma_store_4d(mx, sx, x0, c4, y0, t);
+                            tma_store_4d(mi, si, x0, c4, y0, t);
+                            bulk_commit();
+                        }
                     }
                 }
             }
+            buf ^= 1;
         }
         if (lane == 0) bulk_wait_all();  // every store of this warp has reached global memory
         __syncwarp();
     }
     fence_before();
     __syncthreads();
+    cluster_sync();  // no MMA, copy, store or remote arrive of either CTA is outstanding past this point
     if (warp == 1) {
         fence_after();
-        tmem_dealloc(tmem, SP_TMEM_COLS);
+        tmem_dealloc_pair(tmem, SP_TMEM_COLS);
     }
 }
 
@@ -554,19 +602,6 @@ __device__ __forceinline__ void group_sync(int g)
         bar_sync<2, 32 * PR_GROUP_WARPS>();
 }
 
-__device__ __forceinline__ uint32_t cluster_id()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ uint32_t cluster_count()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
 
 // Where an epilogue group stands: its CTA's rank in the pair, the cluster's item
 // sequence, and the even CTA's hand-off barriers (shared::cluster addresses).
@@ -1634,6 +1669,14 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
             return MCMP2_EUNSUPPORTED;
         }
         plan.pair_clusters = n;
+        cfg.blockDim = dim3(SP_THREADS);
+        cfg.dynamicSmemBytes = SP_SMEM;
+        n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, spinor_mixed_kernel, &cfg) != cudaSuccess || n < 1) {
+            err = "the spinor kernel's CTA pairs cannot be resident on this device";
+            return MCMP2_EUNSUPPORTED;
+        }
+        plan.spinor_clusters = n;
     }
     plan.ready = true;
     return MCMP2_OK;
@@ -1647,9 +1690,6 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
         err = "mixed path not prepared";
         return MCMP2_ENOTLOADED;
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int *flag = reinterpret_cast<int *>(ws + L.flag);
     auto bf = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(ws + off); };
 
@@ -1662,8 +1702,24 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     const int n_mt = (L.P + 127) / 128;
     SpinorArgs sa{scale, flag, L.P, s.n_l, n_mt, L.n_kb, L.n_kb_occ, s.n_occ, s.n_vir, s.n_orb, s.n_tau,
                   plan.tf32 ? 1 : 0, plan.ncomp};
-    const int sp_tiles = n_mt * plan.ncomp * L.n_kb;
-    spinor_mixed_kernel<<<sp_tiles < sms ? sp_tiles : sms, SP_THREADS, SP_SMEM, st>>>(smaps, sa);
+    const int sp_units = (n_mt + 1) / 2 * (plan.ncomp / 2) * L.n_kb;  // (position block pair, component pair, kb)
+    const int sp_clusters = sp_units < plan.spinor_clusters ? sp_units : plan.spinor_clusters;
+    cudaLaunchAttribute sp_attr[1];
+    sp_attr[0].id = cudaLaunchAttributeClusterDimension;
+    sp_attr[0].val.clusterDim.x = 2;
+    sp_attr[0].val.clusterDim.y = 1;
+    sp_attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t sp_cfg = {};
+    sp_cfg.gridDim = dim3(2 * sp_clusters);
+    sp_cfg.blockDim = dim3(SP_THREADS);
+    sp_cfg.dynamicSmemBytes = SP_SMEM;
+    sp_cfg.stream = st;
+    sp_cfg.attrs = sp_attr;
+    sp_cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&sp_cfg, spinor_mixed_kernel, smaps, sa) != cudaSuccess) {
+        err = "spinor formation launch failed";
+        return MCMP2_ECUDA;
+    }
 
     PairMaps pmaps;
     std::memcpy(&pmaps.occ, plan.maps_pairs[0], sizeof(CUtensorMap));

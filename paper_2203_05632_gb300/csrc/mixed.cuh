@@ -29,6 +29,7 @@ struct MixedPlan {
     unsigned long long withhold_once_ns = 0;  // test hook for the bounded-wait path (see mcmp2_test_stall_next)
     alignas(64) unsigned char maps_spinor[12][128];  // 8 loads of spinor formation, 4 stores of X and i X
     int pair_clusters = 0;  // CTA pairs of the contraction resident at once (its persistent grid)
+    int spinor_clusters = 0;  // CTA pairs of the spinor formation resident at once
     alignas(64) unsigned char maps_pairs[4][128];  // X and i X, occupied and virtual
 };
 

@@ -249,6 +249,20 @@ __device__ __forceinline__ uint32_t cluster_rank()
     return r;
 }
 
+__device__ __forceinline__ uint32_t cluster_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_count()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
 // Address, in the shared::cluster window, of the same variable in CTA `rank` of the cluster.
 __device__ __forceinline__ uint32_t mapa_shared(const void *p, uint32_t rank)
 {
