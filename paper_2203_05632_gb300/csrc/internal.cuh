@@ -78,25 +78,6 @@ __device__ __forceinline__ double u53_half_open(uint32_t a, uint32_t b)
     return __dmul_rn(v, 1.0 / 9007199254740992.0);
 }
 
-// Weight function g(r) of Eq. basisSet, with c N(zeta) folded on the host.
-// Every operation is rounded as written (no contraction) so that the walk is
-// reproducible from the same counters on any IEEE machine up to exp().
-__device__ __forceinline__ double weight_g(const DevSystem &s, double x, double y, double z)
-{
-    double g = 0.0;
-    for (int i = 0; i < s.n_centres; ++i) {
-        const double dx = __dsub_rn(x, s.centres[3 * i + 0]);
-        const double dy = __dsub_rn(y, s.centres[3 * i + 1]);
-        const double dz = __dsub_rn(z, s.centres[3 * i + 2]);
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        const double *w = s.wcoef + 4 * i;
-        const double t1 = __dmul_rn(w[0], exp(__dmul_rn(-w[1], d2)));
-        const double t2 = __dmul_rn(w[2], exp(__dmul_rn(-w[3], d2)));
-        g = __dadd_rn(g, __dadd_rn(t1, t2));
-    }
-    return g;
-}
-
 // Optional record of the per-element values of one tile of the pair-of-pairs sum
 // (mcmp2_debug_elements): for the tile (bp, bq) of tp x tp walker pairs,
 // out[(t tp + i) tp + j] = Re f/(w w w) of p = bp tp + i, q = bq tp + j at time t

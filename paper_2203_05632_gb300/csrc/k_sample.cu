@@ -12,12 +12,15 @@ namespace mcmp2 {
 // g is FP64-exp bound on GB300, so its terms are spread over the block: one
 // thread per (pair, position, centre) evaluates that centre's two Gaussians at
 // one of the pair's four positions (old and proposed r1, r2), and one thread per
-// pair then adds the centres in order (the rounding of weight_g) and decides the
+// pair then adds the centres in index order (every operation rounded as written,
+// no contraction, so the same counters give the same walk on the host) and decides the
 // move.  The pair's weight factor a_p = N_g / (g(r1) g(r2)) at the resulting
 // positions is written as well (a may be null).
 constexpr int MET_PAIRS = 4;     // walker pairs per block
 constexpr int MET_THREADS = 128;
 
+// Centre i's two Gaussians of the weight function g(r) of Eq. basisSet at (x, y, z),
+// with c N(zeta) folded on the host; every operation is rounded as written.
 __device__ __forceinline__ double centre_term(const DevSystem &s, int i, double x, double y, double z)
 {
     const double dx = __dsub_rn(x, s.centres[3 * i + 0]);
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(MET_THREADS) metropolis_kernel(DevSystem s, do
         if (p < s.m) {
             double g[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {  // centres added in order, as weight_g does
+            for (int j = 0; j < 4; ++j) {  // g = sum over the centres in index order
                 double v = 0.0;
                 for (int i = 0; i < nc; ++i) v = __dadd_rn(v, terms[lp * per_pair + j * nc + i]);
                 g[j] = v;
@@ -105,15 +108,35 @@ __global__ void __launch_bounds__(MET_THREADS) metropolis_kernel(DevSystem s, do
     if (threadIdx.x == 0 && sacc) atomicAdd(accepted, (unsigned long long)sacc);  // one atomic per block
 }
 
-// a_p = N_g / (g(r1p) g(r2p)): with 1/(w w) this is the weight factor of a pair of pairs.
-__global__ void pair_weights_kernel(DevSystem s, const double *__restrict__ r, double *__restrict__ a)
+// a_p = N_g / (g(r1p) g(r2p)): with 1/(w w) this is the weight factor of a pair of
+// pairs.  As in the Metropolis kernel, one thread per (pair, position, centre)
+// evaluates that centre's Gaussians and one thread per pair adds the centres in
+// index order, with the Metropolis kernel's rounding.
+constexpr int PW_PAIRS = 8;  // walker pairs per block
+constexpr int PW_THREADS = 128;
+__global__ void __launch_bounds__(PW_THREADS) pair_weights_kernel(DevSystem s, const double *__restrict__ r,
+                                                                  double *__restrict__ a)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= s.m) return;
-    const double *r1 = r + 6 * p, *r2 = r1 + 3;
-    const double g1 = weight_g(s, r1[0], r1[1], r1[2]);
-    const double g2 = weight_g(s, r2[0], r2[1], r2[2]);
-    a[p] = s.Ng / (g1 * g2);
+    extern __shared__ double pw_terms[];  // [PW_PAIRS][2][n_centres]
+    const int nc = s.n_centres;
+    const int p0 = blockIdx.x * PW_PAIRS;
+    const int per_pair = 2 * nc;
+    for (int w = threadIdx.x; w < PW_PAIRS * per_pair; w += PW_THREADS) {
+        const int lp = w / per_pair, rem = w - lp * per_pair;
+        const int j = rem / nc, i = rem - j * nc;
+        if (p0 + lp < s.m) {
+            const double *x = r + 6 * (p0 + lp) + 3 * j;
+            pw_terms[w] = centre_term(s, i, x[0], x[1], x[2]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < PW_PAIRS && p0 + threadIdx.x < s.m) {
+        const double *t = pw_terms + threadIdx.x * per_pair;
+        double g1 = 0.0, g2 = 0.0;
+        for (int i = 0; i < nc; ++i) g1 = __dadd_rn(g1, t[i]);
+        for (int i = 0; i < nc; ++i) g2 = __dadd_rn(g2, t[nc + i]);
+        a[p0 + threadIdx.x] = __ddiv_rn(s.Ng, __dmul_rn(g1, g2));
+    }
 }
 
 // Imaginary times and propagator scales for one step.  Block t handles time t:
@@ -211,8 +234,8 @@ cudaError_t launch_metropolis(const DevSystem &s, double *r, const unsigned long
 
 cudaError_t launch_pair_weights(const DevSystem &s, const double *r, double *a, cudaStream_t st)
 {
-    const int threads = 32;
-    pair_weights_kernel<<<(s.m + threads - 1) / threads, threads, 0, st>>>(s, r, a);
+    const size_t smem = sizeof(double) * PW_PAIRS * 2 * s.n_centres;  // 256 centres: 32 KB
+    pair_weights_kernel<<<(s.m + PW_PAIRS - 1) / PW_PAIRS, PW_THREADS, smem, st>>>(s, r, a);
     return cudaGetLastError();
 }
 

@@ -758,12 +758,15 @@ int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const doub
         CK(cudaMemcpyAsync(out + s0, slots, sizeof(double) * len, cudaMemcpyDeviceToHost, st), "copy results");
         CK(cudaStreamSynchronize(st), "replay sync");
     }
-    if (ctx->precision != MCMP2_FP64) {
-        const int rc = mixed_check_flag(ctx->L.mixed, ctx->ws, st, ctx->err);
-        if (rc) return rc;
-    }
     for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(out[i])) return ctx->fail(MCMP2_ENONFINITE, "step %lld is not finite", (long long)i);
+        if (!std::isfinite(out[i])) {
+            // A step whose kernels gave up on a wait reports NaN: name the time-out if that is why.
+            if (ctx->precision != MCMP2_FP64) {
+                const int rc = mixed_check_flag(ctx->L.mixed, ctx->ws, st, ctx->err);
+                if (rc) return rc;
+            }
+            return ctx->fail(MCMP2_ENONFINITE, "step %lld is not finite", (long long)i);
+        }
     return MCMP2_OK;
 }
 
