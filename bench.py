@@ -63,7 +63,8 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms during the timed region
+    (start() returns once the first sample has arrived, so sampling covers the region)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -75,7 +76,7 @@ class ClockSampler:
         self.gpu_id = gpu_id
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20"]
         if self.gpu_id is not None:
             cmd += ["-i", str(self.gpu_id)]
         try:
@@ -85,6 +86,9 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t0 = time.time()
+        while not self.rows and self.proc.poll() is None and time.time() - t0 < 5.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -348,8 +352,12 @@ def measure_rank(args, rank, world, local, barrier):
     clocks.start()
     barrier()
     torch.cuda.synchronize()
-    ctx.profile(1)
+    # The timed steps replay the step graph exactly as run_steps does; a second pass
+    # of the same length, whose graph holds events around the contraction, gives
+    # the kernel's own time.
     dev_ms = time_steps(ctx, torch, args.steps, seed, flush)
+    ctx.profile(1)
+    time_steps(ctx, torch, args.steps, seed, flush)
     prof = ctx.profile(0)
     ctx.profile(2)  # timing off again
     torch.cuda.synchronize()
@@ -416,8 +424,9 @@ def measure_rank(args, rank, world, local, barrier):
             fctx.set_interaction(inter if interaction is None else interaction)
             fctx.set_walkers(synthetic.walker_positions(system.centres, 1, m_run, seed=seed)[0], seed, 200)
             fctx.run_steps(3 if p != pkg.MCMP2_FP64 else 1, seed)
-            fctx.profile(1)
             f_ms = time_steps(fctx, torch, steps, seed, flush)
+            fctx.profile(1)
+            time_steps(fctx, torch, steps, seed, flush)
             fp = fctx.profile(0)
             fctx.close()
             f_pair = fp["pair_ms"] / max(1, fp["pair_launches"])
