@@ -51,6 +51,20 @@ def test_mixed_replay_matches_oracle_tiny(tiny, tiny_oracle, m, n_tau):
     assert np.all(_steps_ok(tiny_oracle, r, tau, got, want)), (got, want)
 
 
+@pytest.mark.parametrize("prec", [pkg.MCMP2_MIXED, pkg.MCMP2_TF32])
+def test_spinor_units_with_an_odd_position_block_count(medium, medium_oracle, prec):
+    """m = 136: 272 positions are three 128-position blocks (the last one ragged), so
+    the spinor formation's second CTA pair owns the third block and a phantom fourth
+    whose rows are zero-filled and never stored."""
+    m, n_tau = 136, 1
+    r = synthetic.walker_positions(medium.centres, 1, m, seed=137)
+    tau = synthetic.imaginary_times(medium_oracle.lam(), 1, n_tau, seed=138)
+    ctx = pkg.Context(medium, m, n_tau, prec)
+    got = ctx.eval_fixed(r, tau)
+    want = medium_oracle.eval_steps(r, tau)
+    assert np.all(_steps_ok(medium_oracle, r, tau, got, want, prec)), (got, want)
+
+
 def test_mixed_replay_matches_oracle_medium_system(medium, medium_oracle):
     m, n_tau = 40, 2
     r = synthetic.walker_positions(medium.centres, 1, m, seed=41)
