@@ -136,6 +136,18 @@ def test_two_component_tensor_forms_match_oracle_tiny(tiny2c, tiny2c_oracle, pre
     assert np.all(_steps_ok(tiny2c_oracle, r, tau, got, want, prec)), (got, want)
 
 
+def test_two_component_spinor_units_with_an_odd_position_block_count(medium2c, medium2c_oracle):
+    """m = 136: three 128-position blocks, so the spinor formation's second CTA pair
+    owns a ragged block and a phantom one (two-component units: components 0, 1)."""
+    m, n_tau = 136, 1
+    r = synthetic.walker_positions(medium2c.centres, 1, m, seed=139)
+    tau = synthetic.imaginary_times(medium2c_oracle.lam(), 1, n_tau, seed=140)
+    ctx = pkg.Context(medium2c, m, n_tau, pkg.MCMP2_MIXED)
+    got = ctx.eval_fixed(r, tau)
+    want = medium2c_oracle.eval_steps(r, tau)
+    assert np.all(_steps_ok(medium2c_oracle, r, tau, got, want)), (got, want)
+
+
 def test_two_component_mixed_full_size_sampled_tiles(medium2c, medium2c_oracle):
     m, n_tau = 1024, 4
     r = synthetic.walker_positions(medium2c.centres, 1, m, seed=71)
