@@ -10,6 +10,8 @@
 #include <vector>
 
 #include "../../include/mcmp2.h"
+
+#include <nvtx3/nvToolsExt.h>
 #include "internal.cuh"
 #include "mixed.cuh"
 
@@ -18,6 +20,15 @@ using namespace mcmp2;
 namespace {
 
 constexpr int REPLAY_CHUNK = 16;  // replay-mode steps staged per host->device copy
+
+// A named range around a public call, for profilers that read NVTX ranges
+// (header-only NVTX v3: a no-op unless a tool is attached).
+struct CallRange {
+    explicit CallRange(const char *name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange &) = delete;
+    CallRange &operator=(const CallRange &) = delete;
+};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -481,12 +492,14 @@ extern "C" {
 int mcmp2_load_system(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir, const double *C,
                       const double *eps)
 {
+    CallRange range_("mcmp2_load_system");
     return load_system_impl(ctx, b, n_occ, n_vir, C, eps, 4);
 }
 
 int mcmp2_load_system_2c(mcmp2_ctx *ctx, const mcmp2_basis *b, int n_occ, int n_vir, const double *C2,
                          const double *eps)
 {
+    CallRange range_("mcmp2_load_system_2c");
     if (!ctx) return MCMP2_EINVAL;
     if (ctx->interaction != MCMP2_COULOMB)
         return ctx->fail(MCMP2_EUNSUPPORTED, "the Gaunt / Breit terms need the small components");
@@ -584,6 +597,7 @@ extern "C" {
 
 int mcmp2_set_walkers(mcmp2_ctx *ctx, const double *r_host, uint64_t seed, int64_t burn_in)
 {
+    CallRange range_("mcmp2_set_walkers");
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
     if (burn_in < 0) return ctx->fail(MCMP2_EINVAL, "burn_in < 0");
@@ -630,6 +644,7 @@ int mcmp2_set_walkers(mcmp2_ctx *ctx, const double *r_host, uint64_t seed, int64
 
 int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
 {
+    CallRange range_("mcmp2_run_steps");
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->walkers) return ctx->fail(MCMP2_ENOTLOADED, "walkers not set");
     if (n < 0) return ctx->fail(MCMP2_EINVAL, "n < 0");
@@ -732,6 +747,7 @@ int mcmp2_run_steps(mcmp2_ctx *ctx, int64_t n, uint64_t seed, mcmp2_result *out)
 
 int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double *tau_host, double *out)
 {
+    CallRange range_("mcmp2_eval_fixed");
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
     if (n < 0 || (n > 0 && (!r_host || !tau_host || !out))) return ctx->fail(MCMP2_EINVAL, "bad replay arguments");
@@ -773,6 +789,7 @@ int mcmp2_eval_fixed(mcmp2_ctx *ctx, int64_t n, const double *r_host, const doub
 int mcmp2_backward(mcmp2_ctx *ctx, int64_t n, const double *r_host, const double *tau_host, double *energy_host,
                    double *d_eps_host, double *d_C_host)
 {
+    CallRange range_("mcmp2_backward");
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
     if (ctx->precision != MCMP2_FP64) return ctx->fail(MCMP2_EUNSUPPORTED, "the adjoint runs in the FP64 form");
@@ -907,6 +924,7 @@ int mcmp2_debug_partials(mcmp2_ctx *ctx, double *out, size_t capacity, int *n_ti
 int mcmp2_debug_elements(mcmp2_ctx *ctx, const double *r_host, const double *tau_host, int bp, int bq,
                          double *out_host, size_t capacity, double *step_host, int *tile_pairs)
 {
+    CallRange range_("mcmp2_debug_elements");
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
     const int m = ctx->dims.m, nt = ctx->dims.n_tau, tp = ctx->L.tile_pairs;
@@ -1016,6 +1034,7 @@ int mcmp2_checkpoint_bytes(const mcmp2_ctx *ctx, size_t *bytes)
 
 int mcmp2_checkpoint(mcmp2_ctx *ctx, void *buf, size_t capacity)
 {
+    CallRange range_("mcmp2_checkpoint");
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->walkers) return ctx->fail(MCMP2_ENOTLOADED, "walkers not set");
     size_t need = 0;
@@ -1041,6 +1060,7 @@ int mcmp2_checkpoint(mcmp2_ctx *ctx, void *buf, size_t capacity)
 
 int mcmp2_restore(mcmp2_ctx *ctx, const void *buf, size_t bytes)
 {
+    CallRange range_("mcmp2_restore");
     if (!ctx) return MCMP2_EINVAL;
     if (!ctx->loaded) return ctx->fail(MCMP2_ENOTLOADED, "no system loaded");
     if (!buf || bytes < sizeof(Checkpoint)) return ctx->fail(MCMP2_EINVAL, "checkpoint truncated");
