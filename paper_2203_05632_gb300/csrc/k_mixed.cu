@@ -9,7 +9,8 @@
 //     the spinor values by s_k(tau) for every imaginary time and writes the
 //     BF16 hi/lo planes (or TF32 values) of X(x)_ck = phi_k^c(x) s_k(tau),
 //     rows 4x + c (2x + c for two-component systems), occupied and virtual
-//     orbitals in separate planes, and the same rows of iX = i X.
+//     orbitals in separate planes, and the -im planes of the same rows (with
+//     X's re planes they are the rows of iX = i X, (-im, re)).
 //  3. pairs_mixed_kernel, on CTA pairs: for every (pair tile, tau) the
 //     Hermitian products G(x, y)_cd = sum_k X(x)_ck conj(X(y)_dk) over the
 //     occupied (G-) and virtual (G+) orbitals as M = N = 256 MMAs whose B
@@ -123,7 +124,8 @@ constexpr int SP_THREADS = 64 + 32 * SP_EPI_WARPS;  // TMA warp, MMA (even CTA) 
 constexpr int SP_TMEM_COLS = 512;               // two 256-column accumulators: 2 components x [re | im]
 constexpr int SP_MAX_TAU = 64;                  // scale staging capacity (the API limits n_tau to 64)
 constexpr int SP_BOX_BYTES = 32 * 128;          // one TMA store box: 32 rows x one 128-byte chunk
-constexpr int SP_WARP_STAGE = 2 * SP_BOX_BYTES;  // X and iX boxes of one epilogue warp
+constexpr int SP_NBOX_BYTES = 32 * 64;          // one -im box: 32 rows x one 64-byte chunk
+constexpr int SP_WARP_STAGE = 2 * SP_BOX_BYTES;  // X and -im boxes of one epilogue warp (1 KB aligned)
 constexpr int SP_BARS_OFF = SP_STAGES * SP_STAGE_BYTES;
 constexpr int SP_SCALE_OFF = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16;
 constexpr int SP_WSTAGE_OFF = (SP_SCALE_OFF + SP_MAX_TAU * 64 * 4 + 1023) / 1024 * 1024;  // swizzled boxes: 1 KB aligned
@@ -132,11 +134,12 @@ static_assert(SP_SMEM <= 232448, "spinor kernel exceeds the shared memory of one
 
 struct SpinorMaps {
     CUtensorMap m[12];  // 0..3: A_L hi, A_L lo, B_L hi, B_L lo; 4..7: the same for the gradient part;
-                        // 8, 9: X occupied / virtual (stores); 10, 11: iX occupied / virtual (stores)
+                        // 8, 9: X occupied / virtual (stores); 10, 11: -im occupied / virtual (stores)
 };
 
 // The operand rows X [n_tau][rows][k_pad / 16][128 B] (occupied and virtual) and
-// i X (planes -im, re) are written through the store tensor maps of SpinorMaps.
+// their -im planes [n_tau][rows][k_pad / 16][64 B] are written through the store
+// tensor maps of SpinorMaps.
 struct SpinorArgs {
     const float *scale;   // [n_tau][n_orb]
     int *abort_flag;
@@ -321,17 +324,18 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
         // component's.  Then, for every time and chunk, it stages its 32 rows of the
         // chunk in shared memory in the contraction's operand order (re_hi, re_lo,
         // im_hi, im_lo, 32 B each; or re, im as TF32, 64 B each; 128-byte swizzle), and
-        // the same rows of iX = i X (halves swapped, the new first half negated), and
-        // one lane writes both 4 KB boxes with TMA stores.
+        // the negated im half of the same rows (64 B per row, 64-byte swizzle), and
+        // one lane writes the 4 KB and the 2 KB box with TMA stores.
         const int ew = warp - 2;
         const int quarter = warp & 3;
         const int jh = ew >> 2;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
         float *sscale = reinterpret_cast<float *>(smem + SP_SCALE_OFF);  // [n_tau][64]
         unsigned char *sx = smem + SP_WSTAGE_OFF + ew * SP_WARP_STAGE;   // X box: 32 rows x 128 B
-        unsigned char *si = sx + SP_BOX_BYTES;                          // iX box
+        unsigned char *sn = sx + SP_BOX_BYTES;                          // -im box: 32 rows x 64 B
         const uint32_t neg = args.tf32 ? 0x80000000u : 0x80008000u;    // sign bits of the packed values
         const int sw = lane & 7;                                       // 128-byte swizzle of this lane's row
+        const int sw64 = (lane >> 1) & 3;                              // 64-byte swizzle of this lane's row
         int buf = 0;
         uint32_t ephase[2] = {0, 0};
         for (int jt = 0, slot; (slot = sp_slot(jt, cid, ncl)) < n_units; ++jt) {
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
             const int k_first = (occ ? 0 : args.n_occ) + kl * 64;  // absolute index of the block's first orbital
             const int k_end = occ ? args.n_occ : args.n_orb;       // one past the region's last orbital
             const CUtensorMap *mx = &maps.m[occ ? 8 : 9];
-            const CUtensorMap *mi = &maps.m[occ ? 10 : 11];
+            const CUtensorMap *mn = &maps.m[occ ? 10 : 11];
             for (int i = threadIdx.x - 64; i < 64 * args.n_tau; i += 32 * SP_EPI_WARPS) {
                 const int t = i >> 6, k = k_first + (i & 63);
                 sscale[i] = k < k_end ? args.scale[(size_t)t * args.n_orb + k] : 0.f;
@@ -419,23 +423,26 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
                         __syncwarp();
 #pragma unroll
                         for (int v = 0; v < 8; ++v) {
-                            const int u = (v ^ sw) << 4;  // 128-byte swizzle: 16-byte unit v of row `lane`
-                            uint4 w = d[v ^ 4];
-                            const uint32_t f = v < 4 ? neg : 0u;
-                            w.x ^= f;
-                            w.y ^= f;
-                            w.z ^= f;
-                            w.w ^= f;
-                            *reinterpret_cast<uint4 *>(sx + lane * 128 + u) = d[v];
-                            *reinterpret_cast<uint4 *>(si + lane * 128 + u) = w;
+                            // 128-byte swizzle: 16-byte unit v of row `lane`; the im half (v >= 4)
+                            // also negated into the -im box (64-byte swizzle)
+                            *reinterpret_cast<uint4 *>(sx + lane * 128 + ((v ^ sw) << 4)) = d[v];
+                            if (v >= 4) {
+                                uint4 w = d[v];
+                                w.x ^= neg;
+                                w.y ^= neg;
+                                w.z ^= neg;
+                                w.w ^= neg;
+                                *reinterpret_cast<uint4 *>(sn + lane * 64 + (((v - 4) ^ sw64) << 4)) = w;
+                            }
                         }
                         fence_proxy_async_smem();
                         __syncwarp();
                         const int x0 = kl * 256 + 64 * j, y0 = mt * 128 + 32 * quarter;
                         if (lane == 0 && y0 < args.P) {
-                            // Box {64 elements, 1 component, 32 positions, 1 time}; positions past P are clipped.
+                            // Boxes {64 (X) or 32 (-im) elements, 1 component, 32 positions, 1 time};
+                            // positions past P are clipped.
                             tma_store_4d(mx, sx, x0, c4, y0, t);
-                            tma_store_4d(mi, si, x0, c4, y0, t);
+                            tma_store_4d(mn, sn, x0 / 2, c4, y0, t);
                             bulk_commit();
                         }
                     }
@@ -465,8 +472,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
 // planes of a chunk and the MMA selects a plane by a 32-byte offset.  In the
 // TF32 form the 128 B are re and im of the chunk as TF32 (64 B each); the
 // same offsets then select (re, K 0-7), (re, K 8-15), (im, K 0-7), (im, K 8-15).
-// The i-multiplied rows iX = i X (planes -im, re: each row's two 64-byte
-// halves swapped, the new first half negated) are written beside them.
+// The negated im planes of the same rows (64 B per chunk) are written beside
+// them: with X's re planes they are the rows of iX = i X = (-im, re).
 //
 // The kernel runs on CTA pairs (clusters of two CTAs on the two SMs of a
 // TPC).  Work item = (pair tile, time); a pair tile is two p-blocks x one
@@ -474,7 +481,10 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
 // that a block is 128 operand rows): CTA r owns p-block bp = 2 BP + r, whose
 // 128 rows are its half of the A operand of an M = 256 MMA, and holds the
 // q-block's 128 rows as its half of the B operand, CTA 0 from X and CTA 1 from
-// iX.  One thread of the even CTA issues cta_group::2 MMAs with M = N = 256:
+// iX.  The B half arrives as two 64-byte-swizzled tiles of 128 rows x 64 B: in
+// CTA 0 the re and the im half of X's chunk, in CTA 1 the -im planes and X's re
+// half, so both CTAs' real-plane B sits in the first tile and the imaginary-plane
+// B in the second.  One thread of the even CTA issues cta_group::2 MMAs with M = N = 256:
 // with A = X_re planes and B = [Y; iY]_re planes, then A = X_im and B =
 // [Y; iY]_im, one accumulator of 256 columns collects
 //   [Xr Yr^T + Xi Yi^T | Xi Yr^T - Xr Yi^T] = [Re G | Im G],
@@ -502,7 +512,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1) spinor_mixed_kernel(const __gri
 constexpr int PR_BK = 16;                           // orbitals per chunk (one stage)
 constexpr int PR_TILE_BYTES = 128 * 4 * PR_BK * 2;  // 128 rows x (4 planes x 16 BF16) = 16 KB
 constexpr int PR_STAGES = 4;
-constexpr int PR_STAGE_BYTES = 2 * PR_TILE_BYTES;   // A chunk, then this CTA's B chunk
+constexpr int PR_BTILE_BYTES = 128 * 2 * PR_BK * 2; // 128 rows x (2 planes x 16 BF16) = 8 KB, 64-byte swizzle
+constexpr int PR_STAGE_BYTES = PR_TILE_BYTES + 2 * PR_BTILE_BYTES;  // A chunk, then this CTA's two B tiles
 constexpr int PR_GROUPS = 2;
 constexpr int PR_GROUP_WARPS = 8;                   // two per tensor-memory lane quarter
 constexpr int PR_EPI_WARPS = PR_GROUPS * PR_GROUP_WARPS;
@@ -522,9 +533,11 @@ static_assert(PR_STAGE_BYTES % 1024 == 0, "stages must keep the 1024-byte swizzl
 static_assert((2 * PR_STAGES + 4 * PR_GROUPS) * 8 + 4 <= 192, "barrier block too small");
 
 struct PairMaps {
-    // 3-D (chunk x plane x orbital, row, tau), 128-byte swizzle, 64 x 128-row boxes:
-    // X (occupied, virtual) and iX (occupied, virtual).
-    CUtensorMap occ, vir, iocc, ivir;
+    // 3-D (chunk x plane x orbital, row, tau).  occ, vir: X, 128-byte swizzle, 64 x
+    // 128-row boxes (the A operand); hocc, hvir: X, 64-byte swizzle, 32 x 128-row
+    // boxes (one half of a chunk); nocc, nvir: the -im planes, 64-byte swizzle, 32 x
+    // 128-row boxes.
+    CUtensorMap occ, vir, hocc, hvir, nocc, nvir;
 };
 
 struct PairArgs {
@@ -1258,12 +1271,14 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
     if (warp == 0) {
         // ---------------- TMA producer (both CTAs) ----------------
         if (lane == 0) {
-            const CUtensorMap *b_occ = leader ? &maps.occ : &maps.iocc;  // B half: Y (even CTA) or iY (odd)
-            const CUtensorMap *b_vir = leader ? &maps.vir : &maps.ivir;
+            // B half: Y = (re, im) in the even CTA, iY = (-im, re) in the odd one.
+            const CUtensorMap *b1_occ = leader ? &maps.hocc : &maps.nocc, *b1_vir = leader ? &maps.hvir : &maps.nvir;
             tma_prefetch(&maps.occ);
             tma_prefetch(&maps.vir);
-            tma_prefetch(b_occ);
-            tma_prefetch(b_vir);
+            tma_prefetch(&maps.hocc);
+            tma_prefetch(&maps.hvir);
+            tma_prefetch(b1_occ);
+            tma_prefetch(b1_vir);
             int stage = 0;
             uint32_t phase = 0;
             int issued[PR_STAGES] = {};
@@ -1295,7 +1310,11 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
                 unsigned char *st = smem + stage * PR_STAGE_BYTES;
                 mbar_arrive_expect_tx(&full[stage], PR_STAGE_BYTES);
                 tma_load_3d(st, occ ? &maps.occ : &maps.vir, &full[stage], x, a_row, t);
-                tma_load_3d(st + PR_TILE_BYTES, occ ? b_occ : b_vir, &full[stage], x, b_row, t);
+                // B tile 1 (real planes): X's re half (even CTA) or the -im planes (odd CTA);
+                // B tile 2 (imaginary planes): X's im half (even CTA) or X's re half (odd CTA).
+                tma_load_3d(st + PR_TILE_BYTES, occ ? b1_occ : b1_vir, &full[stage], leader ? x : x / 2, b_row, t);
+                tma_load_3d(st + PR_TILE_BYTES + PR_BTILE_BYTES, occ ? &maps.hocc : &maps.hvir, &full[stage],
+                            leader ? x + 2 * PR_BK : x, b_row, t);
                 issued[stage] = 1;
                 issued_phase[stage] = phase;
                 if (++stage == PR_STAGES) {
@@ -1342,9 +1361,9 @@ __global__ void __launch_bounds__(PR_THREADS, 1) pairs_mixed_kernel(const __grid
             const uint32_t base0 = smem_u32(smem);
             const uint64_t arh0 = sdesc_sw128(base0 + 0), arl0 = sdesc_sw128(base0 + 32);
             const uint64_t aih0 = sdesc_sw128(base0 + 64), ail0 = sdesc_sw128(base0 + 96);
-            constexpr uint32_t BOFF = PR_TILE_BYTES;
-            const uint64_t brh0 = sdesc_sw128(base0 + BOFF + 0), brl0 = sdesc_sw128(base0 + BOFF + 32);
-            const uint64_t bih0 = sdesc_sw128(base0 + BOFF + 64), bil0 = sdesc_sw128(base0 + BOFF + 96);
+            constexpr uint32_t BOFF = PR_TILE_BYTES, BOFF2 = PR_TILE_BYTES + PR_BTILE_BYTES;
+            const uint64_t brh0 = sdesc_sw64(base0 + BOFF + 0), brl0 = sdesc_sw64(base0 + BOFF + 32);
+            const uint64_t bih0 = sdesc_sw64(base0 + BOFF2 + 0), bil0 = sdesc_sw64(base0 + BOFF2 + 32);
             for_each_chunk(cid, ncl, n_items, n_occ_chunks, n_vir_chunks, [&](int li, int, bool occ, int c) {
                 const int g = li & 1;
                 const uint32_t d = tmem + 256u * g;  // [Re G | Im G]
@@ -1472,24 +1491,27 @@ int encode(void *out, void *addr, int rank, const cuuint64_t *dims, const cuuint
 }
 
 // 4-D BF16 tensor map of one operand-row array for the spinor kernel's TMA stores:
-// dims (element of a row, component, position, time), box {64, 1, 32, 1} = one
-// 128-byte chunk of 32 positions' rows, 128-byte swizzle.
-int encode_store(void *out, void *addr, int kpad, int ncomp, int P, int rows, int n_tau, std::string &err)
+// dims (element of a row, component, position, time).  planes = 4 (X: box {64, 1,
+// 32, 1} = one 128-byte chunk of 32 positions' rows, 128-byte swizzle) or 2 (the
+// -im planes: box {32, 1, 32, 1} = one 64-byte chunk, 64-byte swizzle).
+int encode_store(void *out, void *addr, int kpad, int ncomp, int P, int rows, int n_tau, std::string &err,
+                 int planes = 4)
 {
     auto enc = encode_fn();
     if (!enc) {
         err = "cuTensorMapEncodeTiled is not available from the driver";
         return MCMP2_EUNSUPPORTED;
     }
-    const cuuint64_t row_bytes = (cuuint64_t)4 * kpad * 2;
-    const cuuint64_t dims[4] = {(cuuint64_t)4 * kpad, (cuuint64_t)ncomp, (cuuint64_t)P, (cuuint64_t)n_tau};
+    const cuuint64_t row_bytes = (cuuint64_t)planes * kpad * 2;
+    const cuuint64_t dims[4] = {(cuuint64_t)planes * kpad, (cuuint64_t)ncomp, (cuuint64_t)P, (cuuint64_t)n_tau};
     const cuuint64_t strides[3] = {row_bytes, row_bytes * ncomp, row_bytes * rows};
-    const cuuint32_t box[4] = {64u, 1u, 32u, 1u};
+    const cuuint32_t box[4] = {(cuuint32_t)(16 * planes), 1u, 32u, 1u};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUtensorMap map;
     const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, addr, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           planes == 4 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         err = "cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")";
         return MCMP2_ECUDA;
@@ -1531,8 +1553,8 @@ MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t
     L.WTS_lo = take((size_t)L.wt_rows * L.nl3_pad * 2);
     L.occ_planes = take((size_t)n_tau * 4 * L.rows * L.k_occ_pad * 2);
     L.vir_planes = take((size_t)n_tau * 4 * L.rows * L.k_vir_pad * 2);
-    L.occ_iplanes = take((size_t)n_tau * 4 * L.rows * L.k_occ_pad * 2);
-    L.vir_iplanes = take((size_t)n_tau * 4 * L.rows * L.k_vir_pad * 2);
+    L.occ_nplanes = take((size_t)n_tau * 2 * L.rows * L.k_occ_pad * 2);
+    L.vir_nplanes = take((size_t)n_tau * 2 * L.rows * L.k_vir_pad * 2);
     L.flag = take(sizeof(int));
     L.end = off;
     return L;
@@ -1609,21 +1631,28 @@ int mixed_prepare(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, cha
                            err)) ||
         (rc = encode_store(plan.maps_spinor[9], ws + L.vir_planes, L.k_vir_pad, plan.ncomp, L.P, L.rows, L.n_tau,
                            err)) ||
-        (rc = encode_store(plan.maps_spinor[10], ws + L.occ_iplanes, L.k_occ_pad, plan.ncomp, L.P, L.rows, L.n_tau,
-                           err)) ||
-        (rc = encode_store(plan.maps_spinor[11], ws + L.vir_iplanes, L.k_vir_pad, plan.ncomp, L.P, L.rows, L.n_tau,
-                           err)))
+        (rc = encode_store(plan.maps_spinor[10], ws + L.occ_nplanes, L.k_occ_pad, plan.ncomp, L.P, L.rows, L.n_tau,
+                           err, 2)) ||
+        (rc = encode_store(plan.maps_spinor[11], ws + L.vir_nplanes, L.k_vir_pad, plan.ncomp, L.P, L.rows, L.n_tau,
+                           err, 2)))
         return rc;
     {
         const cuuint64_t dO[3] = {(cuuint64_t)4 * L.k_occ_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
         const cuuint64_t sO[2] = {(cuuint64_t)L.k_occ_pad * 8, (cuuint64_t)L.rows * L.k_occ_pad * 8};
         const cuuint64_t dV[3] = {(cuuint64_t)4 * L.k_vir_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
         const cuuint64_t sV[2] = {(cuuint64_t)L.k_vir_pad * 8, (cuuint64_t)L.rows * L.k_vir_pad * 8};
-        const auto sw = CU_TENSOR_MAP_SWIZZLE_128B;
+        // The -im planes: half the row length.
+        const cuuint64_t nO[3] = {(cuuint64_t)2 * L.k_occ_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
+        const cuuint64_t nsO[2] = {(cuuint64_t)L.k_occ_pad * 4, (cuuint64_t)L.rows * L.k_occ_pad * 4};
+        const cuuint64_t nV[3] = {(cuuint64_t)2 * L.k_vir_pad, (cuuint64_t)rows_used, (cuuint64_t)L.n_tau};
+        const cuuint64_t nsV[2] = {(cuuint64_t)L.k_vir_pad * 4, (cuuint64_t)L.rows * L.k_vir_pad * 4};
+        const auto sw = CU_TENSOR_MAP_SWIZZLE_128B, sw64 = CU_TENSOR_MAP_SWIZZLE_64B;
         if ((rc = encode(plan.maps_pairs[0], ws + L.occ_planes, 3, dO, sO, err, 4 * PR_BK, sw)) ||
             (rc = encode(plan.maps_pairs[1], ws + L.vir_planes, 3, dV, sV, err, 4 * PR_BK, sw)) ||
-            (rc = encode(plan.maps_pairs[2], ws + L.occ_iplanes, 3, dO, sO, err, 4 * PR_BK, sw)) ||
-            (rc = encode(plan.maps_pairs[3], ws + L.vir_iplanes, 3, dV, sV, err, 4 * PR_BK, sw)))
+            (rc = encode(plan.maps_pairs[2], ws + L.occ_planes, 3, dO, sO, err, 2 * PR_BK, sw64)) ||
+            (rc = encode(plan.maps_pairs[3], ws + L.vir_planes, 3, dV, sV, err, 2 * PR_BK, sw64)) ||
+            (rc = encode(plan.maps_pairs[4], ws + L.occ_nplanes, 3, nO, nsO, err, 2 * PR_BK, sw64)) ||
+            (rc = encode(plan.maps_pairs[5], ws + L.vir_nplanes, 3, nV, nsV, err, 2 * PR_BK, sw64)))
             return rc;
     }
     if (cudaFuncSetAttribute(spinor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM) !=
@@ -1724,8 +1753,10 @@ int mixed_step(MixedPlan &plan, const DevSystem &s, const MixedLayout &L, char *
     PairMaps pmaps;
     std::memcpy(&pmaps.occ, plan.maps_pairs[0], sizeof(CUtensorMap));
     std::memcpy(&pmaps.vir, plan.maps_pairs[1], sizeof(CUtensorMap));
-    std::memcpy(&pmaps.iocc, plan.maps_pairs[2], sizeof(CUtensorMap));
-    std::memcpy(&pmaps.ivir, plan.maps_pairs[3], sizeof(CUtensorMap));
+    std::memcpy(&pmaps.hocc, plan.maps_pairs[2], sizeof(CUtensorMap));
+    std::memcpy(&pmaps.hvir, plan.maps_pairs[3], sizeof(CUtensorMap));
+    std::memcpy(&pmaps.nocc, plan.maps_pairs[4], sizeof(CUtensorMap));
+    std::memcpy(&pmaps.nvir, plan.maps_pairs[5], sizeof(CUtensorMap));
     const int nb = pair_blocks(s.m, plan.ncomp == 2 ? TILE_PAIRS_MIXED_2C : TILE_PAIRS_MIXED);
     const int n_tiles = nb * (nb + 1) / 2;
     int n_ptiles = 0;  // pair tiles: two p-blocks x one q-block, q-block >= the first p-block

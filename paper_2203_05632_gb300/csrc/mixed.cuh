@@ -16,7 +16,8 @@ struct MixedLayout {
     size_t BL_hi, BL_lo, BS_hi, BS_lo;      // basis values / gradients, BF16 hi/lo: [P][nl_pad], [P][nl3_pad]
     size_t WTL_hi, WTL_lo, WTS_hi, WTS_lo;  // transposed spinor coefficients, BF16 hi/lo: [wt_rows][nl(3)_pad]
     size_t occ_planes, vir_planes;          // X of all times: [n_tau][rows][k_pad / 16][128 B] (4 BF16 or 2 TF32 planes of 16)
-    size_t occ_iplanes, vir_iplanes;        // i X in the same layout (planes -im, re): the odd CTA's B operand
+    size_t occ_nplanes, vir_nplanes;        // the -im planes of X: [n_tau][rows][k_pad / 16][64 B]; with X's
+                                            // re planes they form i X = (-im, re), the odd CTA's B operand
     size_t flag;                            // time-out flag word
     size_t end;
 };
@@ -27,10 +28,10 @@ struct MixedPlan {
     bool tf32 = false;  // propagator operands as TF32 (re, im) instead of split BF16 (re hi/lo, im hi/lo)
     int ncomp = 4;      // spinor components of the loaded system (2: 32-pair tiles of 2 x 2 blocks)
     unsigned long long withhold_once_ns = 0;  // test hook for the bounded-wait path (see mcmp2_test_stall_next)
-    alignas(64) unsigned char maps_spinor[12][128];  // 8 loads of spinor formation, 4 stores of X and i X
+    alignas(64) unsigned char maps_spinor[12][128];  // 8 loads of spinor formation, 4 stores of X and -im
     int pair_clusters = 0;  // CTA pairs of the contraction resident at once (its persistent grid)
     int spinor_clusters = 0;  // CTA pairs of the spinor formation resident at once
-    alignas(64) unsigned char maps_pairs[4][128];  // X and i X, occupied and virtual
+    alignas(64) unsigned char maps_pairs[6][128];  // occupied / virtual: X rows (A), X halves and -im planes (B)
 };
 
 MixedLayout mixed_layout(int m, int n_l, int n_occ, int n_vir, int n_tau, size_t offset);
