@@ -42,7 +42,7 @@ TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 # by (form, spinor components), from the ncu captures summarised in
 # profiles/pairs_mixed_{bf16x3,tf32,bf16x3_2c}_medium_m1024.md (the kernels as
 # they stand; None where no capture of the current kernel exists).
-PAIRS_TRAFFIC_BYTES = {("mixed", 4): 297.2e6, ("tf32", 4): 297.6e6, ("mixed", 2): 137.3e6}
+PAIRS_TRAFFIC_BYTES = {("mixed", 4): 216.7e6, ("tf32", 4): 215.8e6, ("mixed", 2): 107.9e6}
 
 
 def flops_per_sample(n_occ, n_vir, n_comp=4):
