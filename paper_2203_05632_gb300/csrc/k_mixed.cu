@@ -126,6 +126,7 @@ constexpr int SP_MAX_TAU = 64;                  // scale staging capacity (the A
 constexpr int SP_BOX_BYTES = 32 * 128;          // one TMA store box: 32 rows x one 128-byte chunk
 constexpr int SP_NBOX_BYTES = 32 * 64;          // one -im box: 32 rows x one 64-byte chunk
 constexpr int SP_WARP_STAGE = 2 * SP_BOX_BYTES;  // X and -im boxes of one epilogue warp (1 KB aligned)
+static_assert(SP_BOX_BYTES + SP_NBOX_BYTES <= SP_WARP_STAGE, "a warp's X and -im boxes share its stage");
 constexpr int SP_BARS_OFF = SP_STAGES * SP_STAGE_BYTES;
 constexpr int SP_SCALE_OFF = SP_BARS_OFF + (2 * SP_STAGES + 4) * 8 + 16;
 constexpr int SP_WSTAGE_OFF = (SP_SCALE_OFF + SP_MAX_TAU * 64 * 4 + 1023) / 1024 * 1024;  // swizzled boxes: 1 KB aligned
